@@ -1,0 +1,237 @@
+"""Pins of the oracle's time integration: STS and BE on eigenmodes (closed-form amplification),
+the PTL (Eq. 5) on an eigenmode and on a spike, the dynamic cycle loop on an eigenmode, the
+Fig. 1 set-up, conservation on the sphere, and dense eigen-decomposition / Cholesky truth."""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg
+from scipy.special import eval_gegenbauer, eval_legendre
+
+import synth
+from oracle.advance import be_advance, sts_advance
+from oracle.dense import apply_function, dense_matrix, symmetric_eig
+from oracle.geometry import Shell
+from oracle.pcg import be_solve
+from oracle.ptl import ptl
+from oracle.sts import rkg2_stages, rkl2_stages
+from oracle.tc import TCOperator
+from oracle.visc import ViscOperator
+from periodic import mode, tc_box, tc_symbol, visc_box, visc_symbol
+
+
+def R_closed(scheme, s, z):
+    if scheme == "rkl2":
+        b = (s * s + s - 2.0) / (2.0 * s * (s + 1.0))
+        return (1 - b) + b * eval_legendre(s, 1.0 + 4.0 / (s * s + s - 2.0) * z)
+    b = 4.0 * (s - 1.0) * (s + 4.0) / (3.0 * s * (s + 1.0) * (s + 2.0) * (s + 3.0))
+    a = 1.0 - b * (s + 1.0) * (s + 2.0) / 2.0
+    return a + b * eval_gegenbauer(s, 1.5, 1.0 + 6.0 / ((s + 4.0) * (s - 1.0)) * z)
+
+
+STAGES = {"rkl2": rkl2_stages, "rkg2": rkg2_stages}
+
+
+@pytest.mark.parametrize("scheme", ["rkl2", "rkg2"])
+@pytest.mark.parametrize("m", [(1, 0, 0), (2, 1, 3), (5, 3, 2)])
+def test_sts_step_on_eigenmode(scheme, m):
+    shape = (8, 6, 10)
+    b = np.array([0.6, -0.48, 0.64])
+    op = tc_box(shape, b, kappa=1.7)
+    u, th = mode(shape, m)
+    lam = tc_symbol(th, b, kappa=1.7)
+    dt = 37.0 * op.dt_explicit()
+    un, log = sts_advance(op, u, dt, scheme, use_ptl=False)
+    s = STAGES[scheme](dt / op.dt_explicit())
+    assert log.s == [s]
+    np.testing.assert_allclose(un, R_closed(scheme, s, dt * lam) * u, atol=1e-13)
+
+
+@pytest.mark.parametrize("m", [(1, 0, 0), (2, 1, 3), (5, 3, 4)])
+def test_be_step_on_eigenmode(m):
+    shape = (8, 6, 10)
+    op = visc_box(shape)
+    u1, th = mode(shape, m)
+    u = np.concatenate([u1, 2 * u1, -u1])
+    lam = visc_symbol(th)
+    dt = 250.0 * op.dt_explicit()
+    un, log = be_advance(op, u, dt, use_ptl=False, rtol=1e-14, max_iter=500)
+    np.testing.assert_allclose(un, u / (1.0 - dt * lam), atol=1e-12)
+
+
+def test_ptl_on_eigenmode_is_inverse_eigenvalue():
+    """F = lambda u, so every qualifying neighbour gives -du/dF = -1/lambda."""
+    shape = (8, 6, 10)
+    b = np.array([0.36, 0.48, 0.8])
+    op = tc_box(shape, b)
+    u, th = mode(shape, (2, 1, 1))
+    lam = tc_symbol(th, b)
+    dtp, k, fmax = ptl(op, u, op.apply(u))
+    assert dtp == pytest.approx(-1.0 / lam, rel=1e-12)
+    assert fmax == pytest.approx(abs(lam) * np.abs(u).max(), rel=1e-12)
+
+
+def test_ptl_on_spikes():
+    """Unit spike: a 1-D spike (the plane i = 4, constant in theta and phi) under the 3-point
+    Laplacian (bhat along r) gives dt_PTL = h^2/3 = (2/3) dt_E; a point spike under the 3-D
+    7-point Laplacian gives 1/7 = (6/7) dt_E."""
+    op = tc_box((5, 5, 9), (1.0, 0.0, 0.0))
+    u = np.zeros(op.shape); u[:, :, 4] = 1.0; u = u.reshape(-1)
+    dtp, k, _ = ptl(op, u, op.apply(u))
+    assert k == 4
+    assert dtp == pytest.approx(1.0 / 3.0, rel=1e-14)
+    assert dtp == pytest.approx(2.0 / 3.0 * op.dt_explicit(), rel=1e-14)
+    vop = visc_box((5, 5, 9))
+    v = np.zeros(vop.n); v[vop.offsets[1] + 4 + 9 * (2 + 5 * 2)] = 1.0
+    dtp, k, _ = ptl(vop, v, vop.apply(v))
+    assert k == vop.offsets[1] + 4 + 9 * (2 + 5 * 2)
+    assert dtp == pytest.approx(1.0 / 7.0, rel=1e-14)
+
+
+def test_ptl_no_candidate_is_infinite_and_ties_pick_first():
+    op = visc_box((4, 4, 4))
+    u = np.zeros(op.n)
+    dtp, k, fmax = ptl(op, u, op.apply(u))
+    assert dtp == math.inf and k == 0 and fmax == 0.0
+
+
+@pytest.mark.parametrize("scheme", ["rkl2", "rkg2"])
+def test_cycle_loop_on_eigenmode(scheme):
+    """On an eigenmode the PTL stays 1/|lambda| after every cycle (the mode only scales), so the
+    loop takes n = ceil(dt |lambda|) equal cycles and returns R_s(dt_c lambda)^n u."""
+    shape = (8, 6, 10)
+    b = np.array([0.36, 0.48, 0.8])
+    op = tc_box(shape, b)
+    u, th = mode(shape, (1, 1, 0))
+    lam = tc_symbol(th, b)
+    assert 1.0 / abs(lam) > op.dt_explicit()          # above the floor
+    # ~10 cycles: over many more, rounding-level components of faster-decaying-under-R modes
+    # grow relative to the mode and the PTL drifts (a property of the schemes, not of the loop)
+    dt = 9.3 / abs(lam)
+    un, log = sts_advance(op, u, dt, scheme, use_ptl=True)
+    n = math.ceil(dt * abs(lam))
+    assert log.cycles == n
+    dt_c = dt / n
+    s = STAGES[scheme](dt_c / op.dt_explicit())
+    assert set(log.s) == {s}
+    np.testing.assert_allclose(log.dt_c, dt_c, rtol=1e-10)
+    np.testing.assert_allclose(un, R_closed(scheme, s, dt_c * lam) ** n * u, atol=1e-12)
+    # BE takes the same schedule and gives (1 - dt_c lambda)^-n
+    ub, logb = be_advance(op, u, dt, use_ptl=True, rtol=1e-14)
+    assert logb.cycles == n
+    np.testing.assert_allclose(ub, u / (1.0 - dt_c * lam) ** n, atol=1e-11)
+
+
+def test_cycle_floor_at_explicit_limit():
+    """Where the PTL is below dt_E (the spike) the cycle length is floored at dt_E; with the
+    floor removed the literal rule cycles at dt_PTL."""
+    op = tc_box((5, 5, 9), (1.0, 0.0, 0.0))
+    u = np.zeros(op.shape); u[:, :, 4] = 1.0; u = u.reshape(-1)
+    dtE = op.dt_explicit()
+    _, log = sts_advance(op, u, 3.0 * dtE, "rkl2", use_ptl=True)
+    assert log.dt_c[0] == pytest.approx(dtE, rel=1e-14)
+    _, log0 = sts_advance(op, u, 3.0 * dtE, "rkl2", use_ptl=True, floor=0.0, max_cycles=1000)
+    assert log0.dt_c[0] == pytest.approx(dtE * 3.0 / 5.0, rel=1e-14)   # ceil(3 / (2/3)) = 5
+
+
+def test_fig1_amplification_factors():
+    """Fig. 1 (middle, right): 1-D uniform heat equation, second-order central differences,
+    dt = 500 dt_E.  Mode amplification of RKL2, RKG2 and BE from the oracle against
+    R_s(z), 1/(1-z), with z = -1000 sin^2(theta/2); RKG2's high-mode amplification saturates
+    lower and varies less than RKL2's; BE damps more weakly than exp(z) at high modes."""
+    N = 64
+    op = tc_box((3, 3, N), (1.0, 0.0, 0.0))
+    dtE = op.dt_explicit()
+    dt = 500.0 * dtE
+    amps = {}
+    ms = np.arange(1, N // 2 + 1)
+    for scheme in ("rkl2", "rkg2", "be"):
+        g = []
+        for m in ms:
+            u, th = mode(op.shape, (m, 0, 0), phase=0.0)
+            if scheme == "be":
+                un, _ = be_advance(op, u, dt, use_ptl=False, rtol=1e-14, max_iter=1000)
+            else:
+                un, _ = sts_advance(op, u, dt, scheme, use_ptl=False)
+            g.append(un @ u / (u @ u))
+        amps[scheme] = np.array(g)
+    z = -1000.0 * np.sin(np.pi * ms / N) ** 2
+    np.testing.assert_allclose(amps["rkl2"], R_closed("rkl2", rkl2_stages(500.0), z), atol=1e-12)
+    np.testing.assert_allclose(amps["rkg2"], R_closed("rkg2", rkg2_stages(500.0), z), atol=1e-12)
+    np.testing.assert_allclose(amps["be"], 1.0 / (1.0 - z), rtol=1e-10)
+    hi = ms > N // 4
+    assert np.abs(amps["rkg2"][hi]).max() < np.abs(amps["rkl2"][hi]).max()
+    assert np.std(amps["rkg2"][hi]) < np.std(amps["rkl2"][hi])
+    assert np.all(amps["be"][hi] > np.exp(z[hi]))
+
+
+def _sphere_tc(shape=(6, 5, 8), seed=11):
+    n_r, n_t, n_p = shape
+    g = synth.make_grid(n_r, n_t, n_p, 1.2)
+    inp = synth.tc_inputs(g, seed, noise=0.2, m=synth.random_unit_vector(np.random.default_rng(seed)))
+    sh = Shell(g.r_face, g.t_face, g.n_phi)
+    return TCOperator.spherical(sh, inp.T, inp.n, inp.B), inp.T.reshape(-1)
+
+
+def _sphere_visc(shape=(6, 5, 8), seed=11):
+    n_r, n_t, n_p = shape
+    g = synth.make_grid(n_r, n_t, n_p, 1.2)
+    vi = synth.visc_inputs(g, seed)
+    sh = Shell(g.r_face, g.t_face, g.n_phi)
+    return ViscOperator.spherical(sh, vi.rho, vi.nu), np.concatenate([a.reshape(-1) for a in vi.v])
+
+
+@pytest.mark.parametrize("kind", ["tc", "visc"])
+@pytest.mark.parametrize("scheme", ["rkl2", "rkg2"])
+def test_sts_matches_dense_polynomial_and_conserves(kind, scheme):
+    op, u = _sphere_tc() if kind == "tc" else _sphere_visc()
+    dtE = op.dt_explicit()
+    dt = 60.0 * dtE
+    un, log = sts_advance(op, u, dt, scheme, use_ptl=False)
+    s = log.s[0]
+    exact = apply_function(op, lambda lam: R_closed(scheme, s, dt * lam), u)
+    np.testing.assert_allclose(un, exact, atol=1e-12 * np.abs(u).max())
+    M = 1.0 / op.w
+    assert (M * un).sum() == pytest.approx((M * u).sum(), rel=1e-13)
+    # with PTL cycling too
+    up, logp = sts_advance(op, u, dt, scheme, use_ptl=True)
+    assert (M * up).sum() == pytest.approx((M * u).sum(), rel=1e-13)
+    assert sum(logp.dt_c) == pytest.approx(dt, rel=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["tc", "visc"])
+def test_be_pcg_matches_cholesky(kind):
+    op, u = _sphere_tc() if kind == "tc" else _sphere_visc()
+    dt = 300.0 * op.dt_explicit()
+    A = dense_matrix(op.apply_A, op.n)
+    S = np.diag(1.0 / op.w) - dt * A
+    x_exact = scipy.linalg.cho_solve(scipy.linalg.cho_factor(S), u / op.w)
+    res = be_solve(op, u, dt, rtol=1e-14, max_iter=2000)
+    assert res.converged and res.true_rel_residual < 1e-13
+    np.testing.assert_allclose(res.x, x_exact, rtol=1e-10, atol=1e-11 * np.abs(x_exact).max())
+    # and equals exp-free BE through the eigen-decomposition
+    np.testing.assert_allclose(res.x, apply_function(op, lambda lam: 1.0 / (1.0 - dt * lam), u),
+                               atol=1e-10 * np.abs(u).max())
+
+
+def test_be_positivity_isotropic():
+    """S = M - dt A is an M-matrix for the isotropic operator: BE keeps u >= 0 for any dt."""
+    op, _ = _sphere_visc()
+    u = np.random.default_rng(5).uniform(0.0, 1.0, op.n)
+    for ratio in (1.0, 100.0, 1e4):
+        res = be_solve(op, u, ratio * op.dt_explicit(), rtol=1e-14, max_iter=5000)
+        assert res.x.min() >= -1e-12
+
+
+def test_pcg_fixed_iterations_reduce_residual_monotonically_in_energy():
+    op, u = _sphere_tc()
+    dt = 300.0 * op.dt_explicit()
+    errs = []
+    A = dense_matrix(op.apply_A, op.n)
+    S = np.diag(1.0 / op.w) - dt * A
+    x_exact = np.linalg.solve(S, u / op.w)
+    for n in range(1, 12):
+        x = be_solve(op, u, dt, 0.0, 0, fixed_iters=n).x
+        e = x - x_exact
+        errs.append(e @ S @ e)
+    assert all(errs[i + 1] <= errs[i] * (1 + 1e-12) for i in range(len(errs) - 1))
