@@ -1,0 +1,177 @@
+/*
+ * parabolic.h -- C ABI of libparabolic, a GB300 (sm_103a) library that advances the
+ * operator-split parabolic operators of a thermodynamic MHD model over one time step under the
+ * practical time-step limit (PTL) of Caplan et al., "Advancing parabolic operators in
+ * thermodynamic MHD models II" (arXiv:2403.01004).
+ *
+ * Operators (Sec. 2, Eq. 2):
+ *   PB_TC_ANISO  field-aligned thermal conduction  F(T) = C/n div(kappa bb . grad T),
+ *                kappa = T0^{5/2} lagged (frozen for the step), C = (gamma-1)/2 with
+ *                gamma = 5/3 (m_p/k, kappa_0 and the f_c, f_m profiles folded to 1).
+ *   PB_VISC_ISO  artificial viscosity F(v) = (1/rho) div(nu rho grad v) on each of the three
+ *                staggered velocity components.
+ * Schemes (Sec. 3.1, Appendix A): RKL2 / RKG2 super time stepping, and Backward Euler solved by
+ * point-Jacobi (PC1) preconditioned conjugate gradients.
+ * Cycling (Sec. 2, Eqs. 3-5 and the paragraph after Eq. 5): before every cycle the PTL is taken at
+ * k = argmax |F| over the six orthogonal neighbours; the remaining time is split into
+ * n = ceil(t_rem / max(dt_PTL, floor dt_E)) cycles and the next cycle has length t_rem / n.
+ *
+ * Discretisation (the paper gives none): finite volumes on a spherical shell (r, theta, phi),
+ * phi periodic, zero-flux boundaries at r_min, r_max and the poles.  Conduction uses a symmetric
+ * corner ("dual cell") scheme with 27-point support; viscosity a 7-point flux form.  dt_E is
+ * 2 / max_i (sum_j |L_ij|) (Gershgorin bound on the spectral radius of L).
+ *
+ * Memory layout: every field is a dense array of n_r * n_theta * n_phi values with r fastest:
+ * flat index i + n_r * (j + n_theta * k).  A conduction state is one such array (cells).
+ * A viscosity state is the three components back to back: v_r on (n_r-1) x n_theta x n_phi
+ * interior r faces, v_theta on n_r x (n_theta-1) x n_phi interior theta faces, v_phi on
+ * n_r x n_theta x n_phi phi faces.  parabolic_state_size() returns the total length.
+ *
+ * Conventions: all device pointers are CUDA device memory of the current device; all work is
+ * enqueued on the stream given to parabolic_setup; every call returns after its work is done
+ * (the host reads small scalars back), except where stated.  A context is not thread safe;
+ * separate contexts are independent.  Every function returns a PB_* status; on failure
+ * pb_last_error() describes it and the caller's arrays hold the last completed cycle.
+ * There is no CPU fallback: without a usable GB300 every call fails with PB_ECUDA.
+ */
+#ifndef PARABOLIC_H
+#define PARABOLIC_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PB_API __attribute__((visibility("default")))
+#else
+#define PB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define PB_OK            0
+#define PB_EINVAL        1  /* bad argument (size, pointer, option)                        */
+#define PB_ENOMEM        2  /* device or pinned host allocation failed                      */
+#define PB_ECUDA         3  /* CUDA runtime / launch error                                  */
+#define PB_ENOCONVERGE   4  /* PCG hit max_iter before reaching rtol                        */
+#define PB_EMAXCYCLES    5  /* the PTL asked for more than max_cycles cycles                */
+#define PB_ENONFINITE    6  /* a NaN / Inf appeared in F or in a PCG scalar                 */
+#define PB_ETIMEOUT      7  /* a bounded device-side wait ran out                           */
+#define PB_ENOTSUP       8  /* combination not supported by this build                      */
+
+typedef enum { PB_FP64 = 0, PB_FP32 = 1, PB_BF16_STORE = 2 } pb_precision;
+typedef enum { PB_TC_ANISO = 0, PB_VISC_ISO = 1 } pb_op_kind;
+typedef enum { PB_RKL2 = 0, PB_RKG2 = 1 } pb_scheme;
+
+typedef struct pb_ctx pb_ctx;
+
+/* Grid: faces of the spherical shell; phi is uniform with n_phi cells over 2 pi.
+ * Requires n_r >= 2, n_theta >= 2, n_phi >= 3, 0 < r_face increasing,
+ * 0 <= t_face <= pi increasing.  Both arrays are host memory, read during setup only. */
+typedef struct {
+    int32_t n_r, n_theta, n_phi;
+    const double* r_face;   /* n_r + 1 */
+    const double* t_face;   /* n_theta + 1 */
+} pb_grid;
+
+/* Operator inputs (device memory, float64, read during setup only; may be freed afterwards).
+ * PB_TC_ANISO: T0 and n at cells; B (B_r, B_theta, B_phi) at corners, corner [i,j,k] being the
+ *   vertex (r_face[i+1], t_face[j+1], (k+1) dphi); corners with i = n_r-1 or j = n_theta-1 are
+ *   not used.  C multiplies the divergence (1/3 for gamma = 5/3).
+ * PB_VISC_ISO: rho[c] and nu[c] at the points of velocity component c (layout above). */
+typedef struct {
+    int32_t kind;            /* pb_op_kind */
+    double C;
+    const double* T0;
+    const double* n;
+    const double* B[3];
+    const double* rho[3];
+    const double* nu[3];
+} pb_operator;
+
+/* Options of an advance call.  pb_advance_opts_init() fills the defaults. */
+typedef struct {
+    int32_t scheme;           /* PB_RKL2 (default) or PB_RKG2; STS only                     */
+    int32_t use_ptl;          /* 1 (default): cycle under the PTL; 0: one cycle of length dt */
+    int32_t max_cycles;       /* default 100000                                             */
+    double ptl_floor;         /* cycle-length floor in units of dt_E (default 1; 0 = none)  */
+    const double* dt_cycles;  /* host; forced cycle lengths (overrides use_ptl) or NULL     */
+    int32_t n_forced;
+    double rtol;              /* BE: ||b - S x||_2 <= rtol ||b||_2, default 1e-10           */
+    int32_t max_iter;         /* BE: PCG iteration cap per solve, default 100000            */
+    int32_t fixed_iters;      /* BE: > 0 runs exactly this many iterations, no stop test    */
+    int32_t check_every;      /* BE: iterations launched between host convergence checks   */
+} pb_advance_opts;
+
+/* Statistics of an advance call (host struct).  The per-cycle arrays are optional caller-owned
+ * host arrays of length cycle_capacity (records beyond the capacity are dropped). */
+typedef struct {
+    int32_t cycles;
+    int32_t status_cycle;      /* cycle index at which a failure happened, or -1            */
+    int64_t total_stages;      /* STS: sum of s over cycles                                 */
+    int64_t total_iters;       /* BE: sum of PCG iterations over cycles                     */
+    double dt_explicit;
+    double last_dt_ptl;
+    double fmax;
+    int64_t k_index;
+    double final_rel_residual; /* BE: recursive ||r|| / ||b|| of the last solve             */
+    int32_t cycle_capacity;
+    double* dt_cycle;          /* cycle lengths                                             */
+    int32_t* work_cycle;       /* STS stages s, or PCG iterations, per cycle                */
+    double* dt_ptl_cycle;      /* PTL value before each cycle (NaN when not evaluated)      */
+    int64_t* k_cycle;          /* argmax |F| location before each cycle (-1 when not)       */
+} pb_stats;
+
+/* Fills *opts with the defaults listed above. */
+PB_API void pb_advance_opts_init(pb_advance_opts* opts);
+
+/* Human-readable text for a status code (static storage). */
+PB_API const char* pb_status_string(int status);
+
+/* Text of the last error on ctx, or of the last failed parabolic_setup when ctx is NULL
+ * (thread-local).  Valid until the next call on the same context. */
+PB_API const char* pb_last_error(const pb_ctx* ctx);
+
+/* Builds a context: validates the grid, allocates its device workspace (owned by the context),
+ * computes the frozen operator coefficients in float64 on the device (lagged kappa, Sec. 2) and
+ * stores them in the context precision, and reduces dt_E.  precision: PB_FP64, PB_FP32 (float
+ * state and arithmetic; PTL and PCG reductions in float64) or PB_BF16_STORE (bfloat16 state,
+ * float coefficients and arithmetic).  cuda_stream is a cudaStream_t (NULL = legacy default). */
+PB_API int parabolic_setup(const pb_grid* grid, const pb_operator* op, int32_t precision,
+                    void* cuda_stream, pb_ctx** out);
+
+/* Frees the context and its device workspace.  NULL is accepted. */
+PB_API int parabolic_destroy(pb_ctx* ctx);
+
+/* Length of the state vector (elements) and the element size in bytes (8, 4 or 2). */
+PB_API int parabolic_state_size(const pb_ctx* ctx, int64_t* n_elems, int32_t* elem_bytes);
+
+/* The explicit (forward Euler) stable step dt_E of the operator (Appendix A's Delta t_Euler). */
+PB_API int parabolic_dt_explicit(const pb_ctx* ctx, double* dt_e);
+
+/* F = L u for a device state u (ctx precision); F is device memory of the same length. */
+PB_API int parabolic_apply(pb_ctx* ctx, const void* u_dev, void* F_dev);
+
+/* PTL of state u (Eq. 5): dt_ptl (+INF if no neighbour qualifies), the flat index k of
+ * max |F| (ties: smallest index) and |F_k|.  Any output pointer may be NULL. */
+PB_API int ptl_compute(pb_ctx* ctx, const void* u_dev, double* dt_ptl, int64_t* k_index,
+                double* fmax);
+
+/* Advances u (device, in place, ctx precision) over dt with RKL2 or RKG2 super time stepping
+ * (opts->scheme) under PTL cycling (Appendix A stage loop).  stats may be NULL. */
+PB_API int rkl2_advance(pb_ctx* ctx, void* u_dev, double dt, const pb_advance_opts* opts,
+                 pb_stats* stats);
+
+/* Advances u (device, in place) over dt with Backward Euler, each cycle solving
+ * (M - dt_c A) x = M u (M = diag(1/w), F = w A u) by point-Jacobi PCG from x0 = u, or from
+ * x0_dev (device, ctx precision) on the first cycle when it is not NULL.  Supported for
+ * PB_FP64 and PB_FP32 (float vectors, float64 dot products).  stats may be NULL. */
+PB_API int be_pcg_advance(pb_ctx* ctx, void* u_dev, double dt, const pb_advance_opts* opts,
+                   const void* x0_dev, pb_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PARABOLIC_H */

@@ -16,7 +16,10 @@ def centres(faces: np.ndarray) -> np.ndarray:
 
 
 class Shell:
-    def __init__(self, r_face, t_face, n_phi: int):
+    """`dphi` defaults to 2 pi / n_phi; an explicit value describes a phi window of a larger grid
+    (the window is then closed periodically, which only changes points near its phi ends)."""
+
+    def __init__(self, r_face, t_face, n_phi: int, dphi: float | None = None):
         self.r_face = np.asarray(r_face, dtype=np.float64)
         self.t_face = np.asarray(t_face, dtype=np.float64)
         self.n_r = len(self.r_face) - 1
@@ -26,7 +29,7 @@ class Shell:
             raise ValueError("need n_r >= 2, n_theta >= 2, n_phi >= 3")
         self.r_c = centres(self.r_face)
         self.t_c = centres(self.t_face)
-        self.dphi = 2.0 * np.pi / self.n_p
+        self.dphi = 2.0 * np.pi / self.n_p if dphi is None else float(dphi)
         self.shape = (self.n_p, self.n_t, self.n_r)
 
     def cell_volume(self) -> np.ndarray:

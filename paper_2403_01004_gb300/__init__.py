@@ -1,0 +1,308 @@
+"""GB300 (sm_103a) solvers for the operator-split parabolic operators of a thermodynamic MHD model
+under the practical time-step limit (PTL) of arXiv:2403.01004.
+
+This package is a thin ctypes binding over the C ABI of `libparabolic.so` (declared in
+`include/parabolic.h`): argument marshalling only -- every step of the computation runs in the
+library's CUDA kernels.  PyTorch tensors supply device memory and the CUDA stream.  There is no
+CPU fallback: if the library has not been built, or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from ctypes import POINTER, byref, c_double, c_int32, c_int64, c_void_p
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "lib", "libparabolic.so")
+
+PB_OK, PB_EINVAL, PB_ENOMEM, PB_ECUDA, PB_ENOCONVERGE, PB_EMAXCYCLES, PB_ENONFINITE, PB_ETIMEOUT, PB_ENOTSUP = range(9)
+PB_FP64, PB_FP32, PB_BF16_STORE = 0, 1, 2
+PB_TC_ANISO, PB_VISC_ISO = 0, 1
+PB_RKL2, PB_RKG2 = 0, 1
+
+PRECISIONS = {"fp64": PB_FP64, "fp32": PB_FP32, "bf16": PB_BF16_STORE}
+SCHEMES = {"rkl2": PB_RKL2, "rkg2": PB_RKG2}
+C_TC = (5.0 / 3.0 - 1.0) / 2.0
+
+# C function names exported by the library (kept in step with include/parabolic.h)
+EXPORTS = ("pb_advance_opts_init", "pb_status_string", "pb_last_error", "parabolic_setup",
+           "parabolic_destroy", "parabolic_state_size", "parabolic_dt_explicit", "parabolic_apply",
+           "ptl_compute", "rkl2_advance", "be_pcg_advance")
+
+
+class PbGrid(ctypes.Structure):
+    _fields_ = [("n_r", c_int32), ("n_theta", c_int32), ("n_phi", c_int32),
+                ("r_face", POINTER(c_double)), ("t_face", POINTER(c_double))]
+
+
+class PbOperator(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("C", c_double), ("T0", c_void_p), ("n", c_void_p),
+                ("B", c_void_p * 3), ("rho", c_void_p * 3), ("nu", c_void_p * 3)]
+
+
+class PbAdvanceOpts(ctypes.Structure):
+    _fields_ = [("scheme", c_int32), ("use_ptl", c_int32), ("max_cycles", c_int32),
+                ("ptl_floor", c_double), ("dt_cycles", POINTER(c_double)), ("n_forced", c_int32),
+                ("rtol", c_double), ("max_iter", c_int32), ("fixed_iters", c_int32),
+                ("check_every", c_int32)]
+
+
+class PbStats(ctypes.Structure):
+    _fields_ = [("cycles", c_int32), ("status_cycle", c_int32), ("total_stages", c_int64),
+                ("total_iters", c_int64), ("dt_explicit", c_double), ("last_dt_ptl", c_double),
+                ("fmax", c_double), ("k_index", c_int64), ("final_rel_residual", c_double),
+                ("cycle_capacity", c_int32), ("dt_cycle", POINTER(c_double)),
+                ("work_cycle", POINTER(c_int32)), ("dt_ptl_cycle", POINTER(c_double)),
+                ("k_cycle", POINTER(c_int64))]
+
+
+class ParabolicError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"[{status}] {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libparabolic.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    lib.pb_advance_opts_init.argtypes = [POINTER(PbAdvanceOpts)]
+    lib.pb_advance_opts_init.restype = None
+    lib.pb_status_string.argtypes = [c_int32]
+    lib.pb_status_string.restype = ctypes.c_char_p
+    lib.pb_last_error.argtypes = [c_void_p]
+    lib.pb_last_error.restype = ctypes.c_char_p
+    lib.parabolic_setup.argtypes = [POINTER(PbGrid), POINTER(PbOperator), c_int32, c_void_p, POINTER(c_void_p)]
+    lib.parabolic_destroy.argtypes = [c_void_p]
+    lib.parabolic_state_size.argtypes = [c_void_p, POINTER(c_int64), POINTER(c_int32)]
+    lib.parabolic_dt_explicit.argtypes = [c_void_p, POINTER(c_double)]
+    lib.parabolic_apply.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.ptl_compute.argtypes = [c_void_p, c_void_p, POINTER(c_double), POINTER(c_int64), POINTER(c_double)]
+    lib.rkl2_advance.argtypes = [c_void_p, c_void_p, c_double, POINTER(PbAdvanceOpts), POINTER(PbStats)]
+    lib.be_pcg_advance.argtypes = [c_void_p, c_void_p, c_double, POINTER(PbAdvanceOpts), c_void_p, POINTER(PbStats)]
+    for name in ("parabolic_setup", "parabolic_destroy", "parabolic_state_size", "parabolic_dt_explicit",
+                 "parabolic_apply", "ptl_compute", "rkl2_advance", "be_pcg_advance"):
+        getattr(lib, name).restype = c_int32
+    _lib = lib
+    return lib
+
+
+def _check(status: int, ctx_handle=None):
+    if status != PB_OK:
+        lib = load_library()
+        msg = lib.pb_last_error(ctx_handle).decode() if lib.pb_last_error(ctx_handle) else ""
+        raise ParabolicError(status, f"{lib.pb_status_string(status).decode()}: {msg}")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t) -> int:
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream_handle(stream) -> int:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Context:
+    """An operator set up on a grid (owns the library context and its device workspace)."""
+
+    def __init__(self, handle, kind, precision, stream, n, elem):
+        self.handle = handle
+        self.kind = kind
+        self.precision = precision
+        self.stream = stream
+        self.n = n
+        self.elem = elem
+
+    @property
+    def dtype(self):
+        torch = _torch()
+        return {PB_FP64: torch.float64, PB_FP32: torch.float32, PB_BF16_STORE: torch.bfloat16}[self.precision]
+
+    def close(self):
+        if self.handle:
+            load_library().parabolic_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def parabolic_setup(r_face, t_face, n_phi: int, kind: str, fields: dict, precision: str = "fp64",
+                    C: float = C_TC, stream=None) -> Context:
+    """Builds a context.  kind = "tc" with fields T0, n, B (3 tensors at corners), or kind = "visc"
+    with fields rho, nu (lists of 3 tensors); fields are float64 CUDA tensors."""
+    lib = load_library()
+    torch = _torch()
+    rf = (c_double * len(r_face))(*[float(x) for x in r_face])
+    tf = (c_double * len(t_face))(*[float(x) for x in t_face])
+    g = PbGrid(len(r_face) - 1, len(t_face) - 1, int(n_phi), ctypes.cast(rf, POINTER(c_double)),
+               ctypes.cast(tf, POINTER(c_double)))
+    op = PbOperator()
+    keep = []
+
+    def dptr(t):
+        if t.dtype != torch.float64:
+            raise TypeError("operator fields must be float64")
+        keep.append(t)
+        return _ptr(t)
+
+    if kind == "tc":
+        op.kind = PB_TC_ANISO
+        op.C = float(C)
+        op.T0 = dptr(fields["T0"])
+        op.n = dptr(fields["n"])
+        for a in range(3):
+            op.B[a] = dptr(fields["B"][a])
+    elif kind == "visc":
+        op.kind = PB_VISC_ISO
+        for a in range(3):
+            op.rho[a] = dptr(fields["rho"][a])
+            op.nu[a] = dptr(fields["nu"][a])
+    else:
+        raise ValueError(kind)
+    h = c_void_p()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib.parabolic_setup(byref(g), byref(op), PRECISIONS[precision], c_void_p(_stream_handle(st)), byref(h)))
+    n = c_int64()
+    e = c_int32()
+    _check(lib.parabolic_state_size(h, byref(n), byref(e)), h)
+    return Context(h, kind, PRECISIONS[precision], st, n.value, e.value)
+
+
+def parabolic_dt_explicit(ctx: Context) -> float:
+    v = c_double()
+    _check(load_library().parabolic_dt_explicit(ctx.handle, byref(v)), ctx.handle)
+    return v.value
+
+
+def _check_state(ctx: Context, u):
+    if u.numel() != ctx.n or u.dtype != ctx.dtype:
+        raise ValueError(f"state must have {ctx.n} elements of {ctx.dtype}")
+
+
+def parabolic_apply(ctx: Context, u, F=None):
+    """F = L u (device tensors of the context precision)."""
+    _check_state(ctx, u)
+    if F is None:
+        F = _torch().empty_like(u)
+    _check(load_library().parabolic_apply(ctx.handle, c_void_p(_ptr(u)), c_void_p(_ptr(F))), ctx.handle)
+    return F
+
+
+def ptl_compute(ctx: Context, u):
+    """Returns (dt_PTL, k, |F_k|) for state u (Eq. 5)."""
+    _check_state(ctx, u)
+    dt, k, fm = c_double(), c_int64(), c_double()
+    _check(load_library().ptl_compute(ctx.handle, c_void_p(_ptr(u)), byref(dt), byref(k), byref(fm)), ctx.handle)
+    return dt.value, k.value, fm.value
+
+
+def _opts(scheme="rkl2", use_ptl=True, max_cycles=0, ptl_floor=1.0, forced=None, rtol=1e-10,
+          max_iter=100000, fixed_iters=0, check_every=8):
+    lib = load_library()
+    o = PbAdvanceOpts()
+    lib.pb_advance_opts_init(byref(o))
+    o.scheme = SCHEMES[scheme]
+    o.use_ptl = 1 if use_ptl else 0
+    o.max_cycles = int(max_cycles)
+    o.ptl_floor = float(ptl_floor)
+    keep = None
+    if forced is not None:
+        keep = (c_double * len(forced))(*[float(x) for x in forced])
+        o.dt_cycles = ctypes.cast(keep, POINTER(c_double))
+        o.n_forced = len(forced)
+    o.rtol = float(rtol)
+    o.max_iter = int(max_iter)
+    o.fixed_iters = int(fixed_iters)
+    o.check_every = int(check_every)
+    return o, keep
+
+
+class _StatsBuf:
+    def __init__(self, cap: int):
+        self.cap = cap
+        self.dt = (c_double * cap)()
+        self.work = (c_int32 * cap)()
+        self.dtp = (c_double * cap)()
+        self.k = (c_int64 * cap)()
+        self.st = PbStats()
+        self.st.cycle_capacity = cap
+        self.st.dt_cycle = ctypes.cast(self.dt, POINTER(c_double))
+        self.st.work_cycle = ctypes.cast(self.work, POINTER(c_int32))
+        self.st.dt_ptl_cycle = ctypes.cast(self.dtp, POINTER(c_double))
+        self.st.k_cycle = ctypes.cast(self.k, POINTER(c_int64))
+
+    def as_dict(self) -> dict:
+        s = self.st
+        n = min(s.cycles, self.cap)
+        return dict(cycles=s.cycles, total_stages=s.total_stages, total_iters=s.total_iters,
+                    dt_explicit=s.dt_explicit, last_dt_ptl=s.last_dt_ptl, fmax=s.fmax, k_index=s.k_index,
+                    final_rel_residual=s.final_rel_residual, status_cycle=s.status_cycle,
+                    dt_cycle=list(self.dt[:n]), work_cycle=list(self.work[:n]),
+                    dt_ptl_cycle=list(self.dtp[:n]), k_cycle=list(self.k[:n]))
+
+
+def rkl2_advance(ctx: Context, u, dt: float, scheme: str = "rkl2", use_ptl: bool = True,
+                 forced=None, max_cycles: int = 0, ptl_floor: float = 1.0, stats_capacity: int = 4096,
+                 raise_on_error: bool = True) -> dict:
+    """Advances u in place over dt with RKL2 / RKG2 under PTL cycling; returns the statistics."""
+    _check_state(ctx, u)
+    o, keep = _opts(scheme, use_ptl, max_cycles, ptl_floor, forced)
+    sb = _StatsBuf(stats_capacity)
+    rc = load_library().rkl2_advance(ctx.handle, c_void_p(_ptr(u)), float(dt), byref(o), byref(sb.st))
+    d = sb.as_dict()
+    d["status"] = rc
+    if raise_on_error:
+        _check(rc, ctx.handle)
+    return d
+
+
+def be_pcg_advance(ctx: Context, u, dt: float, use_ptl: bool = True, forced=None, rtol: float = 1e-10,
+                   max_iter: int = 100000, fixed_iters: int = 0, x0=None, max_cycles: int = 0,
+                   ptl_floor: float = 1.0, check_every: int = 8, stats_capacity: int = 4096,
+                   raise_on_error: bool = True) -> dict:
+    """Advances u in place over dt with Backward Euler + point-Jacobi PCG under PTL cycling."""
+    _check_state(ctx, u)
+    o, keep = _opts("rkl2", use_ptl, max_cycles, ptl_floor, forced, rtol, max_iter, fixed_iters, check_every)
+    sb = _StatsBuf(stats_capacity)
+    x0p = c_void_p(_ptr(x0)) if x0 is not None else c_void_p(0)
+    rc = load_library().be_pcg_advance(ctx.handle, c_void_p(_ptr(u)), float(dt), byref(o), x0p, byref(sb.st))
+    d = sb.as_dict()
+    d["status"] = rc
+    if raise_on_error:
+        _check(rc, ctx.handle)
+    return d
+
+
+__all__ = ["parabolic_setup", "parabolic_dt_explicit", "parabolic_apply", "ptl_compute", "rkl2_advance",
+           "be_pcg_advance", "Context", "ParabolicError", "load_library", "EXPORTS"]

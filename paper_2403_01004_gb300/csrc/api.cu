@@ -1,0 +1,565 @@
+// C ABI of libparabolic: context set-up, the PTL cycle loop (Sec. 2) around the super-time-
+// stepping stage loop (Appendix A) or Backward Euler + PCG (Sec. 3.1), and the host-side
+// float64 super-time-stepping coefficients.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+
+namespace pb {
+namespace {
+
+thread_local std::string g_setup_error;
+
+// ---- super-time-stepping coefficients (float64, host) ----------------------------------------
+// RKL2 (the Legendre method cited in Sec. 3.1): s = smallest integer >= 2 with
+// (s^2 + s - 2)/4 >= r; b_0 = b_1 = 1/3, b_j = (j^2 + j - 2)/(2 j (j+1)), a_j = 1 - b_j,
+// w1 = 4/(s^2 + s - 2), mut_1 = b_1 w1, mu_j = (2j-1)/j b_j/b_{j-1}, nu_j = -(j-1)/j b_j/b_{j-2},
+// mut_j = mu_j w1, gt_j = -a_{j-1} mut_j.
+// RKG2 (Appendix A, alpha = 3/2): s = ceil(sqrt(25 + 24 r)/2 - 3/2) made odd; b_0 = 1,
+// b_1 = 1/3, b_k = 4(k-1)(k+4)/(3k(k+1)(k+2)(k+3)), w = 6/((s+4)(s-1)), mut_1 = w,
+// mu_k = (2 + 1/k) b_k/b_{k-1}, nu_k = -(1 + 1/k) b_k/b_{k-2}, mut_k = mu_k w,
+// gt_k = (k(k+1)/2 b_{k-1} - 1) mut_k.
+// Both stage counts are evaluated as the integer inequalities (s^2+s-2) >= 4r and
+// (s+4)(s-1) >= 6r so that exact-integer ratios do not round up.
+constexpr long long kMaxStages = 1 << 20;
+
+struct Sts {
+    int s = 0;
+    std::vector<double> mu, nu, mut, gt;
+};
+
+long long stages_rkl2(double r) {
+    long long s = std::max(2LL, (long long)std::ceil((std::sqrt(9.0 + 16.0 * r) - 1.0) / 2.0));
+    while (s > 2 && (double)((s - 1) * (s - 1) + (s - 1) - 2) >= 4.0 * r) --s;
+    while ((double)(s * s + s - 2) < 4.0 * r) ++s;
+    return s;
+}
+
+long long stages_rkg2(double r) {
+    long long s = std::max(2LL, (long long)std::ceil(0.5 * std::sqrt(25.0 + 24.0 * r) - 1.5));
+    while (s > 2 && (double)((s + 3) * (s - 2)) >= 6.0 * r) --s;
+    while ((double)((s + 4) * (s - 1)) < 6.0 * r) ++s;
+    if (s % 2 == 0) ++s;
+    return s;
+}
+
+void coeffs_rkl2(int s, Sts& o) {
+    std::vector<double> b(s + 1);
+    b[0] = b[1] = 1.0 / 3.0;
+    for (int j = 2; j <= s; ++j) b[j] = ((double)j * j + j - 2.0) / (2.0 * j * (j + 1.0));
+    const double w1 = 4.0 / ((double)s * s + s - 2.0);
+    o.s = s;
+    o.mu.assign(s + 1, 0.0); o.nu.assign(s + 1, 0.0); o.mut.assign(s + 1, 0.0); o.gt.assign(s + 1, 0.0);
+    o.mut[1] = b[1] * w1;
+    for (int j = 2; j <= s; ++j) {
+        o.mu[j] = (2.0 * j - 1.0) / j * b[j] / b[j - 1];
+        o.nu[j] = -(j - 1.0) / j * b[j] / b[j - 2];
+        o.mut[j] = o.mu[j] * w1;
+        o.gt[j] = -(1.0 - b[j - 1]) * o.mut[j];
+    }
+}
+
+void coeffs_rkg2(int s, Sts& o) {
+    std::vector<double> b(s + 1);
+    for (int k = 0; k <= s; ++k)
+        b[k] = k == 0 ? 1.0 : k == 1 ? 1.0 / 3.0
+             : 4.0 * (k - 1.0) * (k + 4.0) / (3.0 * k * (k + 1.0) * (k + 2.0) * (k + 3.0));
+    const double w = 6.0 / ((s + 4.0) * (s - 1.0));
+    o.s = s;
+    o.mu.assign(s + 1, 0.0); o.nu.assign(s + 1, 0.0); o.mut.assign(s + 1, 0.0); o.gt.assign(s + 1, 0.0);
+    o.mut[1] = w;
+    for (int k = 2; k <= s; ++k) {
+        o.mu[k] = (2.0 + 1.0 / k) * b[k] / b[k - 1];
+        o.nu[k] = -(1.0 / k + 1.0) * b[k] / b[k - 2];
+        o.mut[k] = o.mu[k] * w;
+        o.gt[k] = (k * (k + 1.0) / 2.0 * b[k - 1] - 1.0) * o.mut[k];
+    }
+}
+
+void make_sts(int scheme, double r, Sts& o) {
+    if (!(r >= 0.0) || std::isinf(r)) throw Error{PB_EINVAL, "dt/dt_E must be finite and >= 0"};
+    const long long s = scheme == PB_RKG2 ? stages_rkg2(r) : stages_rkl2(r);
+    if (s > kMaxStages) throw Error{PB_EINVAL, "stage count above 2^20"};
+    if (scheme == PB_RKG2) coeffs_rkg2((int)s, o);
+    else coeffs_rkl2((int)s, o);
+}
+
+Ops* ops_of(const Ctx& c) {
+    switch (c.prec) {
+        case PB_FP64: return ops_f64();
+        case PB_FP32: return ops_f32();
+        default: return ops_b16();
+    }
+}
+
+// ---- allocation helpers --------------------------------------------------------------------
+void* dmalloc(size_t bytes) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error{PB_ENOMEM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e)};
+    }
+    return p;
+}
+
+void build_grid(Ctx& c) {
+    MarchGrid& g = c.grid;
+    g.ncomp = c.kind == PB_TC_ANISO ? 1 : 3;
+    int dims[3][3];
+    if (c.kind == PB_TC_ANISO) {
+        dims[0][0] = c.nr; dims[0][1] = c.nt; dims[0][2] = c.np;
+    } else {
+        dims[0][0] = c.nr - 1; dims[0][1] = c.nt; dims[0][2] = c.np;
+        dims[1][0] = c.nr; dims[1][1] = c.nt - 1; dims[1][2] = c.np;
+        dims[2][0] = c.nr; dims[2][1] = c.nt; dims[2][2] = c.np;
+    }
+    long long tiles_total = 0;
+    for (int a = 0; a < g.ncomp; ++a)
+        tiles_total += (long long)((dims[a][0] + TX - 1) / TX) * ((dims[a][1] + TY - 1) / TY);
+    // enough phi chunks for ~16 resident tiles per SM, each chunk at least 4 planes long
+    const long long target = (long long)std::max(1, c.sm_count) * 16;
+    int nchunk = (int)std::max(1LL, (target + tiles_total - 1) / tiles_total);
+    nchunk = std::min(nchunk, std::max(1, c.np / 4));
+    const int kchunk = (c.np + nchunk - 1) / nchunk;
+    nchunk = (c.np + kchunk - 1) / kchunk;
+    int64_t off = 0;
+    int blocks = 0;
+    for (int a = 0; a < g.ncomp; ++a) {
+        CompGrid& cg = g.c[a];
+        cg.nr = dims[a][0]; cg.nt = dims[a][1]; cg.np = dims[a][2];
+        cg.tiles_r = (cg.nr + TX - 1) / TX;
+        cg.tiles_t = (cg.nt + TY - 1) / TY;
+        cg.kchunk = kchunk;
+        cg.nchunk = nchunk;
+        cg.offset = off;
+        cg.block_begin = blocks;
+        off += (int64_t)cg.nr * cg.nt * cg.np;
+        blocks += cg.tiles_r * cg.tiles_t * nchunk;
+    }
+    g.nblocks = blocks;
+    c.n = off;
+}
+
+void free_ctx(Ctx& c) {
+    void* ptrs[] = {c.coef, c.coef_be, c.coef64, c.adiag, c.y0, c.buf[0], c.buf[1], c.buf[2], c.r, c.p[0],
+                    c.p[1], c.q, c.dinv, c.partials, c.counter, c.d_ptl, c.d_pcg, c.d_scalar, c.d_flag, c.d_err};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c.h_ptl) cudaFreeHost(c.h_ptl);
+    if (c.h_pcg) cudaFreeHost(c.h_pcg);
+    if (c.h_scalar) cudaFreeHost(c.h_scalar);
+    if (c.h_err) cudaFreeHost(c.h_err);
+}
+
+void ensure_pcg_buffers(Ctx& c) {
+    if (c.r) return;
+    const size_t bytes = (size_t)c.n * c.elem;
+    c.r = dmalloc(bytes);
+    c.p[0] = dmalloc(bytes);
+    c.p[1] = dmalloc(bytes);
+    c.q = dmalloc(bytes);
+    c.dinv = dmalloc(bytes);
+}
+
+// Waits for the context's stream and reports a kernel whose bounded wait ran out.
+void sync(Ctx& c) {
+    PB_CUDA_TRY(cudaMemcpyAsync(c.h_err, c.d_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    PB_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    if (*c.h_err) {
+        *c.h_err = 0;
+        cudaMemsetAsync(c.d_err, 0, sizeof(int), c.stream);
+        cudaStreamSynchronize(c.stream);
+        throw Error{PB_ETIMEOUT, "a kernel's bounded wait for its TMA copies ran out"};
+    }
+}
+
+template <class F>
+int guarded(Ctx* c, F&& f) {
+    try {
+        f();
+        if (c) c->err.clear();
+        return PB_OK;
+    } catch (const Error& e) {
+        if (c) c->err = e.msg; else g_setup_error = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        if (c) c->err = "host allocation failed"; else g_setup_error = "host allocation failed";
+        return PB_ENOMEM;
+    }
+}
+
+pb_advance_opts resolve(const pb_advance_opts* o) {
+    pb_advance_opts r;
+    pb_advance_opts_init(&r);
+    if (o) r = *o;
+    if (r.max_cycles <= 0) r.max_cycles = 100000;
+    if (!(r.ptl_floor >= 0.0)) r.ptl_floor = 1.0;
+    if (!(r.rtol > 0.0)) r.rtol = 1e-10;
+    if (r.max_iter < 0) r.max_iter = 100000;
+    if (r.check_every <= 0) r.check_every = 8;
+    if (r.scheme != PB_RKL2 && r.scheme != PB_RKG2) throw Error{PB_EINVAL, "unknown scheme"};
+    if (r.dt_cycles == nullptr) r.n_forced = 0;
+    if (r.n_forced < 0) throw Error{PB_EINVAL, "n_forced < 0"};
+    return r;
+}
+
+void stats_begin(pb_stats* st, const Ctx& c) {
+    if (!st) return;
+    st->cycles = 0;
+    st->status_cycle = -1;
+    st->total_stages = 0;
+    st->total_iters = 0;
+    st->dt_explicit = c.dt_e;
+    st->last_dt_ptl = std::numeric_limits<double>::quiet_NaN();
+    st->fmax = std::numeric_limits<double>::quiet_NaN();
+    st->k_index = -1;
+    st->final_rel_residual = std::numeric_limits<double>::quiet_NaN();
+}
+
+void stats_cycle(pb_stats* st, double dt_c, int work, double dtp, long long k) {
+    if (!st) return;
+    const int c = st->cycles;
+    if (c < st->cycle_capacity) {
+        if (st->dt_cycle) st->dt_cycle[c] = dt_c;
+        if (st->work_cycle) st->work_cycle[c] = work;
+        if (st->dt_ptl_cycle) st->dt_ptl_cycle[c] = dtp;
+        if (st->k_cycle) st->k_cycle[c] = k;
+    }
+    st->cycles = c + 1;
+}
+
+// Runs the PTL pass on u (y0 = F(u) in c.y0) and returns the result (host).
+PtlResult run_ptl(Ctx& c, Ops* ops, const void* u) {
+    ops->y0_pass(c, u, c.y0, true, nullptr, 0.0);
+    ops->ptl_finalize(c, u, c.y0);
+    PB_CUDA_TRY(cudaMemcpyAsync(c.h_ptl, c.d_ptl, sizeof(PtlResult), cudaMemcpyDeviceToHost, c.stream));
+    sync(c);
+    return *c.h_ptl;
+}
+
+// Decides the next cycle length (Sec. 2): returns false when the step is complete.
+struct CycleState {
+    double dt, t_rem;
+    int c;
+};
+
+}  // namespace
+}  // namespace pb
+
+using namespace pb;
+
+extern "C" {
+
+void pb_advance_opts_init(pb_advance_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->scheme = PB_RKL2;
+    o->use_ptl = 1;
+    o->max_cycles = 100000;
+    o->ptl_floor = 1.0;
+    o->dt_cycles = nullptr;
+    o->n_forced = 0;
+    o->rtol = 1e-10;
+    o->max_iter = 100000;
+    o->fixed_iters = 0;
+    o->check_every = 8;
+}
+
+const char* pb_status_string(int s) {
+    switch (s) {
+        case PB_OK: return "ok";
+        case PB_EINVAL: return "invalid argument";
+        case PB_ENOMEM: return "out of memory";
+        case PB_ECUDA: return "CUDA error";
+        case PB_ENOCONVERGE: return "PCG did not converge";
+        case PB_EMAXCYCLES: return "too many PTL cycles";
+        case PB_ENONFINITE: return "non-finite value";
+        case PB_ETIMEOUT: return "device wait timed out";
+        case PB_ENOTSUP: return "not supported";
+        default: return "unknown status";
+    }
+}
+
+const char* pb_last_error(const pb_ctx* h) {
+    return h ? h->c.err.c_str() : g_setup_error.c_str();
+}
+
+int parabolic_setup(const pb_grid* g, const pb_operator* op, int32_t precision, void* stream, pb_ctx** out) {
+    return guarded(nullptr, [&] {
+        if (!g || !op || !out) throw Error{PB_EINVAL, "null argument"};
+        *out = nullptr;
+        if (g->n_r < 2 || g->n_theta < 2 || g->n_phi < 3) throw Error{PB_EINVAL, "need n_r >= 2, n_theta >= 2, n_phi >= 3"};
+        if (!g->r_face || !g->t_face) throw Error{PB_EINVAL, "null face array"};
+        if (!(g->r_face[0] > 0.0)) throw Error{PB_EINVAL, "r_face[0] must be > 0"};
+        for (int i = 0; i < g->n_r; ++i)
+            if (!(g->r_face[i + 1] > g->r_face[i])) throw Error{PB_EINVAL, "r_face must increase"};
+        if (!(g->t_face[0] >= 0.0) || !(g->t_face[g->n_theta] <= M_PI + 1e-12)) throw Error{PB_EINVAL, "t_face outside [0, pi]"};
+        for (int j = 0; j < g->n_theta; ++j)
+            if (!(g->t_face[j + 1] > g->t_face[j])) throw Error{PB_EINVAL, "t_face must increase"};
+        if ((long long)g->n_r * g->n_theta * g->n_phi > (1LL << 40)) throw Error{PB_EINVAL, "grid too large"};
+        if (precision != PB_FP64 && precision != PB_FP32 && precision != PB_BF16_STORE) throw Error{PB_EINVAL, "bad precision"};
+        if (op->kind == PB_TC_ANISO) {
+            if (!op->T0 || !op->n || !op->B[0] || !op->B[1] || !op->B[2]) throw Error{PB_EINVAL, "conduction needs T0, n, B"};
+            if (!(op->C > 0.0)) throw Error{PB_EINVAL, "C must be > 0"};
+        } else if (op->kind == PB_VISC_ISO) {
+            for (int a = 0; a < 3; ++a)
+                if (!op->rho[a] || !op->nu[a]) throw Error{PB_EINVAL, "viscosity needs rho[3], nu[3]"};
+        } else {
+            throw Error{PB_EINVAL, "unknown operator kind"};
+        }
+        int dev = 0;
+        PB_CUDA_TRY(cudaGetDevice(&dev));
+        pb_ctx* h = new pb_ctx();
+        Ctx& c = h->c;
+        try {
+            c.kind = op->kind;
+            c.prec = precision;
+            c.elem = precision == PB_FP64 ? 8 : precision == PB_FP32 ? 4 : 2;
+            c.stream = static_cast<cudaStream_t>(stream);
+            c.nr = g->n_r; c.nt = g->n_theta; c.np = g->n_phi;
+            PB_CUDA_TRY(cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, dev));
+            build_grid(c);
+            const size_t csz = precision == PB_FP64 ? 8 : 4;
+            c.coef = dmalloc((size_t)c.n * 4 * csz);
+            c.coef_be = dmalloc((size_t)c.n * 4 * csz);
+            c.coef64 = static_cast<Coef4<double>*>(dmalloc((size_t)c.n * sizeof(Coef4<double>)));
+            c.adiag = dmalloc((size_t)c.n * csz);
+            c.y0 = dmalloc((size_t)c.n * c.elem);
+            for (int b = 0; b < 3; ++b) c.buf[b] = dmalloc((size_t)c.n * c.elem);
+            c.partial_cap = std::max(c.grid.nblocks, 3 * reduce_blocks(c)) + 32;
+            c.partials = dmalloc((size_t)c.partial_cap * 32);
+            c.counter = static_cast<unsigned int*>(dmalloc(sizeof(unsigned int)));
+            c.d_ptl = static_cast<PtlResult*>(dmalloc(sizeof(PtlResult)));
+            c.d_pcg = static_cast<PcgScalars*>(dmalloc(sizeof(PcgScalars)));
+            c.d_scalar = static_cast<double*>(dmalloc(sizeof(double)));
+            c.d_flag = static_cast<int*>(dmalloc(sizeof(int)));
+            c.d_err = static_cast<int*>(dmalloc(sizeof(int)));
+            PB_CUDA_TRY(cudaMallocHost(&c.h_err, sizeof(int)));
+            *c.h_err = 0;
+            PB_CUDA_TRY(cudaMemsetAsync(c.d_err, 0, sizeof(int), c.stream));
+            {
+                const char* e = getenv("PB_DISABLE_TMA");
+                c.use_tma = !(e && e[0] == '1');
+            }
+            PB_CUDA_TRY(cudaMallocHost(&c.h_ptl, sizeof(PtlResult)));
+            PB_CUDA_TRY(cudaMallocHost(&c.h_pcg, sizeof(PcgScalars)));
+            PB_CUDA_TRY(cudaMallocHost(&c.h_scalar, sizeof(double)));
+            PB_CUDA_TRY(cudaMemsetAsync(c.counter, 0, sizeof(unsigned int), c.stream));
+            PB_CUDA_TRY(cudaMemsetAsync(c.d_flag, 0, sizeof(int), c.stream));
+            // the float64 diag(A) goes through the PCG residual buffer's slot of y0 / buf space
+            double* adiag64 = static_cast<double*>(dmalloc((size_t)c.n * sizeof(double)));
+            try {
+                if (c.kind == PB_TC_ANISO) setup_tc(c, *g, *op, c.coef64, adiag64, &c.dt_e);
+                else setup_visc(c, *g, *op, c.coef64, adiag64, &c.dt_e);
+                ops_of(c)->store_coefs(c, c.coef64, adiag64);
+                sync(c);
+            } catch (...) {
+                cudaFree(adiag64);
+                throw;
+            }
+            cudaFree(adiag64);
+            if (!(c.dt_e > 0.0) || std::isinf(c.dt_e)) throw Error{PB_ENONFINITE, "dt_E is not a positive finite number"};
+        } catch (...) {
+            free_ctx(c);
+            delete h;
+            throw;
+        }
+        *out = h;
+    });
+}
+
+int parabolic_destroy(pb_ctx* h) {
+    if (!h) return PB_OK;
+    cudaStreamSynchronize(h->c.stream);
+    free_ctx(h->c);
+    delete h;
+    return PB_OK;
+}
+
+int parabolic_state_size(const pb_ctx* h, int64_t* n, int32_t* elem) {
+    if (!h) return PB_EINVAL;
+    if (n) *n = h->c.n;
+    if (elem) *elem = h->c.elem;
+    return PB_OK;
+}
+
+int parabolic_dt_explicit(const pb_ctx* h, double* dt_e) {
+    if (!h || !dt_e) return PB_EINVAL;
+    *dt_e = h->c.dt_e;
+    return PB_OK;
+}
+
+int parabolic_apply(pb_ctx* h, const void* u, void* F) {
+    if (!h) return PB_EINVAL;
+    Ctx& c = h->c;
+    return guarded(&c, [&] {
+        if (!u || !F) throw Error{PB_EINVAL, "null state pointer"};
+        if (u == F) throw Error{PB_EINVAL, "u and F must not alias"};
+        ops_of(c)->apply(c, u, F);
+        sync(c);
+    });
+}
+
+int ptl_compute(pb_ctx* h, const void* u, double* dt_ptl, int64_t* k, double* fmax) {
+    if (!h) return PB_EINVAL;
+    Ctx& c = h->c;
+    return guarded(&c, [&] {
+        if (!u) throw Error{PB_EINVAL, "null state pointer"};
+        const PtlResult r = run_ptl(c, ops_of(c), u);
+        if (r.nonfinite) throw Error{PB_ENONFINITE, "non-finite F in the PTL pass"};
+        if (dt_ptl) *dt_ptl = r.dt_ptl;
+        if (k) *k = r.k;
+        if (fmax) *fmax = r.fmax;
+    });
+}
+
+int rkl2_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, pb_stats* st) {
+    if (!h) return PB_EINVAL;
+    Ctx& c = h->c;
+    stats_begin(st, c);
+    int cycle = 0;
+    const int rc = guarded(&c, [&] {
+        const pb_advance_opts o = resolve(opts);
+        if (!u) throw Error{PB_EINVAL, "null state pointer"};
+        if (!(dt >= 0.0) || std::isinf(dt)) throw Error{PB_EINVAL, "dt must be finite and >= 0"};
+        Ops* ops = ops_of(c);
+        const bool forced = o.n_forced > 0;
+        double t_rem = dt;
+        Sts co;
+        for (cycle = 0;; ++cycle) {
+            double dt_c, dtp = std::numeric_limits<double>::quiet_NaN();
+            long long kk = -1;
+            bool y0_done = false;
+            if (forced) {
+                if (cycle >= o.n_forced) break;
+                dt_c = o.dt_cycles[cycle];
+                if (!(dt_c >= 0.0) || std::isinf(dt_c)) throw Error{PB_EINVAL, "forced cycle length must be finite and >= 0"};
+            } else {
+                if (!(t_rem > 1e-12 * dt)) break;
+                if (cycle >= o.max_cycles) throw Error{PB_EMAXCYCLES, "PTL cycle count above max_cycles"};
+                if (o.use_ptl) {
+                    const PtlResult r = run_ptl(c, ops, u);
+                    if (r.nonfinite) throw Error{PB_ENONFINITE, "non-finite F in the PTL pass"};
+                    dtp = r.dt_ptl;
+                    kk = r.k;
+                    if (st) { st->last_dt_ptl = r.dt_ptl; st->fmax = r.fmax; st->k_index = r.k; }
+                    const double dtl = std::max(dtp, o.ptl_floor * c.dt_e);
+                    const double n = dtl >= t_rem ? 1.0 : std::ceil(t_rem / dtl);
+                    dt_c = t_rem / n;
+                    y0_done = true;
+                } else {
+                    dt_c = t_rem;
+                }
+            }
+            make_sts(o.scheme, dt_c / c.dt_e, co);
+            // stage loop in increment form d_k = u_k - u_0 (see EpiStage): d_1 = mut_1 dt y0 in
+            // buf[0]; buffers rotate over buf[0..2]; the last stage writes u_0 + d_s into u
+            const double a1 = co.mut[1] * dt_c;
+            if (y0_done) ops->stage1(c, c.y0, c.buf[0], a1);
+            else ops->y0_pass(c, u, c.y0, false, c.buf[0], a1);
+            for (int k = 2; k <= co.s; ++k) {
+                const void* dkm1 = c.buf[(k - 2) % 3];
+                const void* dkm2 = k == 2 ? nullptr : c.buf[(k - 3) % 3];
+                const bool last = k == co.s;
+                void* out = last ? u : c.buf[(k - 1) % 3];
+                ops->stage(c, dkm1, dkm2, last ? u : nullptr, c.y0, out,
+                           StageCoef{co.mu[k], co.nu[k], co.mut[k] * dt_c, (co.mut[k] + co.gt[k]) * dt_c});
+            }
+            if (st) st->total_stages += co.s;
+            stats_cycle(st, dt_c, co.s, dtp, kk);
+            t_rem -= dt_c;
+        }
+        sync(c);
+    });
+    if (rc != PB_OK && st) st->status_cycle = cycle;
+    return rc;
+}
+
+int be_pcg_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, const void* x0, pb_stats* st) {
+    if (!h) return PB_EINVAL;
+    Ctx& c = h->c;
+    stats_begin(st, c);
+    int cycle = 0;
+    const int rc = guarded(&c, [&] {
+        const pb_advance_opts o = resolve(opts);
+        if (!u) throw Error{PB_EINVAL, "null state pointer"};
+        if (!(dt >= 0.0) || std::isinf(dt)) throw Error{PB_EINVAL, "dt must be finite and >= 0"};
+        Ops* ops = ops_of(c);
+        if (!ops->supports_pcg()) throw Error{PB_ENOTSUP, "BE + PCG needs PB_FP64 or PB_FP32 storage"};
+        ensure_pcg_buffers(c);
+        const bool forced = o.n_forced > 0;
+        const size_t bytes = (size_t)c.n * c.elem;
+        double t_rem = dt;
+        for (cycle = 0;; ++cycle) {
+            double dt_c, dtp = std::numeric_limits<double>::quiet_NaN();
+            long long kk = -1;
+            if (forced) {
+                if (cycle >= o.n_forced) break;
+                dt_c = o.dt_cycles[cycle];
+                if (!(dt_c >= 0.0) || std::isinf(dt_c)) throw Error{PB_EINVAL, "forced cycle length must be finite and >= 0"};
+            } else {
+                if (!(t_rem > 1e-12 * dt)) break;
+                if (cycle >= o.max_cycles) throw Error{PB_EMAXCYCLES, "PTL cycle count above max_cycles"};
+                if (o.use_ptl) {
+                    const PtlResult r = run_ptl(c, ops, u);
+                    if (r.nonfinite) throw Error{PB_ENONFINITE, "non-finite F in the PTL pass"};
+                    dtp = r.dt_ptl;
+                    kk = r.k;
+                    if (st) { st->last_dt_ptl = r.dt_ptl; st->fmax = r.fmax; st->k_index = r.k; }
+                    const double dtl = std::max(dtp, o.ptl_floor * c.dt_e);
+                    const double n = dtl >= t_rem ? 1.0 : std::ceil(t_rem / dtl);
+                    dt_c = t_rem / n;
+                } else {
+                    dt_c = t_rem;
+                }
+            }
+            // u^n is kept in buf[0]: it is the right-hand side and the state restored on failure
+            PB_CUDA_TRY(cudaMemcpyAsync(c.buf[0], u, bytes, cudaMemcpyDeviceToDevice, c.stream));
+            if (cycle == 0 && x0) PB_CUDA_TRY(cudaMemcpyAsync(u, x0, bytes, cudaMemcpyDeviceToDevice, c.stream));
+            PcgScalars& hs = *c.h_pcg;
+            std::memset(&hs, 0, sizeof(hs));
+            hs.tol2 = o.rtol * o.rtol;
+            hs.max_iter = o.max_iter;
+            hs.fixed = o.fixed_iters > 0 ? o.fixed_iters : 0;
+            hs.dt = dt_c;
+            PB_CUDA_TRY(cudaMemcpyAsync(c.d_pcg, &hs, sizeof(PcgScalars), cudaMemcpyHostToDevice, c.stream));
+            ops->pcg_init(c, u, c.buf[0], dt_c);
+            int parity = 0;
+            for (;;) {
+                PB_CUDA_TRY(cudaMemcpyAsync(c.h_pcg, c.d_pcg, sizeof(PcgScalars), cudaMemcpyDeviceToHost, c.stream));
+                sync(c);
+                if (c.h_pcg->done) break;
+                for (int m = 0; m < o.check_every; ++m) {
+                    ops->pcg_iter(c, u, parity, dt_c);
+                    parity ^= 1;
+                }
+            }
+            const PcgScalars r = *c.h_pcg;
+            if (st) {
+                st->total_iters += r.iter;
+                st->final_rel_residual = r.bb > 0 ? std::sqrt(r.rr / r.bb) : 0.0;
+            }
+            if (r.done != 1) {
+                PB_CUDA_TRY(cudaMemcpyAsync(u, c.buf[0], bytes, cudaMemcpyDeviceToDevice, c.stream));
+                sync(c);
+                if (r.done == 2) throw Error{PB_ENONFINITE, "PCG breakdown or non-finite scalar"};
+                throw Error{PB_ENOCONVERGE, "PCG reached max_iter without meeting rtol"};
+            }
+            stats_cycle(st, dt_c, (int)r.iter, dtp, kk);
+            t_rem -= dt_c;
+        }
+        sync(c);
+    });
+    if (rc != PB_OK && st) st->status_cycle = cycle;
+    return rc;
+}
+
+}  // extern "C"

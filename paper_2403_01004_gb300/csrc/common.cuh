@@ -1,0 +1,144 @@
+// Shared definitions of libparabolic's CUDA translation units: precision policies, the packed
+// coefficient record, grid descriptors, reductions and the context.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/parabolic.h"
+
+namespace pb {
+
+// ---- precision policies -----------------------------------------------------------------
+// S: state storage, C: coefficient storage, A: stencil / stage arithmetic.
+struct PolF64 { using S = double; using C = double; using A = double; static constexpr int id = PB_FP64; };
+struct PolF32 { using S = float; using C = float; using A = float; static constexpr int id = PB_FP32; };
+struct PolB16 { using S = __nv_bfloat16; using C = float; using A = float; static constexpr int id = PB_BF16_STORE; };
+
+template <typename T> __host__ __device__ __forceinline__ float to_f(T v);
+template <> __host__ __device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <typename A, typename T> __device__ __forceinline__ A cvt(T v) { return (A)v; }
+template <> __device__ __forceinline__ float cvt<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ double cvt<double, __nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, float>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, double>(double v) { return __float2bfloat16_rn((float)v); }
+
+// Read-only load of a state element through the non-coherent path.
+template <typename T> __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+template <> __device__ __forceinline__ __nv_bfloat16 ldg<__nv_bfloat16>(const __nv_bfloat16* p) {
+    unsigned short s = __ldg(reinterpret_cast<const unsigned short*>(p));
+    return __ushort_as_bfloat16(s);
+}
+
+// Packed 4-word coefficient record stored at every grid point [i,j,k]:
+//   conduction: {ahat_r, ahat_t, ahat_p} of corner [i,j,k] and the cell weight w of cell [i,j,k]
+//   viscosity : {c_r, c_t, c_p} of the +1 faces of point [i,j,k] and its weight w
+template <typename T> struct alignas(4 * sizeof(T)) Coef4 { T a, b, c, w; };
+
+template <typename A, typename T> __device__ __forceinline__ Coef4<A> load_coef(const Coef4<T>* p);
+template <> __device__ __forceinline__ Coef4<double> load_coef<double, double>(const Coef4<double>* p) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    double2 x = __ldg(q), y = __ldg(q + 1);
+    return Coef4<double>{x.x, x.y, y.x, y.y};
+}
+template <> __device__ __forceinline__ Coef4<float> load_coef<float, float>(const Coef4<float>* p) {
+    float4 x = __ldg(reinterpret_cast<const float4*>(p));
+    return Coef4<float>{x.x, x.y, x.z, x.w};
+}
+
+// ---- grid descriptors ----------------------------------------------------------------------
+// Stencil tiles: TX cells along r (a full warp, coalesced) x TY cells along theta; each block
+// marches through a chunk of consecutive phi planes.
+constexpr int TX = 32;
+constexpr int TY = 8;
+constexpr int NTHREADS = TX * TY;
+
+struct CompGrid {          // one scalar field (a conduction state or one velocity component)
+    int nr, nt, np;
+    int tiles_r, tiles_t, kchunk, nchunk;
+    int64_t offset;        // element offset of this component in the state / coefficient arrays
+    int block_begin;       // first block index of this component in a march launch
+};
+
+struct MarchGrid {
+    int ncomp;
+    CompGrid c[3];
+    int nblocks;
+};
+
+// ---- device-side scalar state ----------------------------------------------------------------
+struct ArgMax { double v; long long i; };
+
+struct PtlResult {
+    double dt_ptl;
+    double fmax;
+    long long k;
+    int nonfinite;
+    int pad;
+};
+
+struct PcgScalars {
+    double rz, rr, bb, pq, alpha, beta, tol2;
+    long long iter, max_iter, fixed;
+    int done;       // 1 converged / finished, 2 breakdown or non-finite, 3 iteration cap
+    int first;
+    double dt;
+};
+
+// ---- context ------------------------------------------------------------------------------
+struct Ctx {
+    int kind = 0, prec = 0;
+    int elem = 8;
+    cudaStream_t stream = nullptr;
+    int nr = 0, nt = 0, np = 0;
+    MarchGrid grid{};
+    int64_t n = 0;                 // state length
+    double dt_e = 0.0;
+    // device workspace
+    void* coef = nullptr;          // Coef4<C>[n], 4th word w (super time stepping, apply, PTL)
+    void* coef_be = nullptr;       // Coef4<C>[n], 4th word M = 1/w (Backward Euler system)
+    Coef4<double>* coef64 = nullptr;  // float64 record (kept for refinement / diagnostics)
+    void* adiag = nullptr;         // diag(A) in C precision [n]
+    void* y0 = nullptr;            // state-typed scratch [n]
+    void* buf[3] = {nullptr, nullptr, nullptr};
+    // PCG vectors (S precision)
+    void* r = nullptr; void* p[2] = {nullptr, nullptr}; void* q = nullptr; void* dinv = nullptr;
+    // reductions
+    void* partials = nullptr;      // max(nblocks, reduce blocks) * 32 bytes
+    int partial_cap = 0;
+    unsigned int* counter = nullptr;
+    PtlResult* d_ptl = nullptr;
+    PcgScalars* d_pcg = nullptr;
+    double* d_scalar = nullptr;    // misc scalar (dt_E)
+    int* d_flag = nullptr;         // non-finite flag
+    int* d_err = nullptr;          // set by a kernel whose bounded wait ran out
+    int* h_err = nullptr;          // pinned mirror
+    bool use_tma = true;
+    // pinned host mirrors
+    PtlResult* h_ptl = nullptr;
+    PcgScalars* h_pcg = nullptr;
+    double* h_scalar = nullptr;
+    std::string err;
+    int sm_count = 0;
+};
+
+struct Error {
+    int code;
+    std::string msg;
+};
+
+}  // namespace pb
+
+struct pb_ctx { pb::Ctx c; };
+
+// Status helpers for host code.
+#define PB_CUDA_TRY(expr)                                                                     \
+    do {                                                                                      \
+        cudaError_t e__ = (expr);                                                             \
+        if (e__ != cudaSuccess)                                                               \
+            throw pb::Error{PB_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e__)};   \
+    } while (0)

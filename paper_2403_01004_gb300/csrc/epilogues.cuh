@@ -1,0 +1,340 @@
+// Loaders and epilogues fused into the march kernels, and the element-wise / finishing kernels
+// of the cycle loop (PTL evaluation, STS stage 1, PCG update).
+#pragma once
+
+#include <climits>
+
+#include "common.cuh"
+#include "march.cuh"
+#include "reduce.cuh"
+
+namespace pb {
+
+struct NoPre {};
+
+// ---- loaders -------------------------------------------------------------------------------
+template <class P>
+struct LoadState {
+    const typename P::S* u;
+    __device__ void init() {}
+    __device__ typename P::A operator()(long long idx) const { return cvt<typename P::A>(ldg(u + idx)); }
+};
+
+// PCG search direction p = z + beta p_old with z = D^-1 r, formed on the fly (halo included).
+template <class P>
+struct LoadPcgP {
+    using A = typename P::A;
+    using S = typename P::S;
+    const S* r;
+    const S* dinv;
+    const S* pold;
+    const PcgScalars* sc;
+    A beta;
+    int first;
+    __device__ void init() {
+        beta = (A)sc->beta;
+        first = sc->first;
+    }
+    __device__ A operator()(long long idx) const {
+        // z is rounded to the state precision exactly as the dot <r, z> sees it
+        const A z = cvt<A>(cvt<S>(cvt<A>(ldg(dinv + idx)) * cvt<A>(ldg(r + idx))));
+        return first ? z : z + beta * cvt<A>(ldg(pold + idx));
+    }
+};
+
+// ---- epilogues -----------------------------------------------------------------------------
+// F = w A u (stored), optionally the stage-1 increment d1 = a F (STS stage 1, see EpiStage)
+// and the block arg-max of |F|.
+template <class P, bool ARGMAX, bool U1>
+struct EpiF {
+    using A = typename P::A;
+    using S = typename P::S;
+    using Pre = NoPre;
+    S* F;
+    S* u1;
+    A a;
+    ArgMax* part;
+    int* nonfinite;
+    double bv;
+    long long bi;
+    int bad;
+    static constexpr int NC = 0;     // point operands delivered by the TMA kernel
+    __device__ void init() { bv = -1.0; bi = LLONG_MAX; bad = 0; }
+    __device__ bool skip() const { return false; }
+    __device__ Pre prefetch(long long) const { return {}; }
+    __device__ void apply_c(long long idx, A Au, A w, A center, A, A, A) { apply(idx, Au, w, center, Pre{}); }
+    __device__ void apply(long long idx, A Au, A w, A center, const Pre&) {
+        const A f = w * Au;
+        const S fs = cvt<S>(f);
+        F[idx] = fs;
+        if (U1) u1[idx] = cvt<S>(a * f);
+        if (ARGMAX) {
+            const double v = fabs((double)cvt<A>(fs));
+            if (!(v <= 1.79769313486231570e308)) bad = 1;
+            else argmax_merge(bv, bi, v, idx);
+        }
+    }
+    __device__ void finish() {
+        if (!ARGMAX) return;
+        if (bad) atomicOr(nonfinite, 1);
+        block_argmax(bv, bi);
+        if (threadIdx.x == 0 && threadIdx.y == 0) part[blockIdx.x] = ArgMax{bv, bi};
+    }
+};
+
+// STS stage k >= 2 (Appendix A) in increment form.  With the frozen (linear) operator,
+// F(u_0 + d) = y_0 + F(d), so the stage recurrence for d_k = u_k - u_0 reads
+//   d_k = mu d_{k-1} + nu d_{k-2} + mut dt F(d_{k-1}) + (mut + gt) dt y_0,   d_0 = 0,
+// which is algebraically the stage update u_k = mu u_{k-1} + nu u_{k-2} + (1-mu-nu) u_0
+// + mut dt F(u_{k-1}) + gt dt y_0; it drops the u_0 read from every stage but the last and
+// keeps stored stage values small (the rounding of reduced-precision storage acts on d, not u).
+// The last stage writes u_s = u_0 + d_s over u_0 in place (each point is read before it is
+// written, by the same thread).
+template <class P, bool KM2, bool LAST>
+struct EpiStage {
+    using A = typename P::A;
+    using S = typename P::S;
+    struct Pre { A dkm2, y0, u0; };
+    const S* dkm2;
+    const S* y0;
+    const S* u0;
+    S* out;
+    A mu, nu, mdt, ydt;
+    // point operands of the TMA kernel, in this order: y0, d_{k-2} (KM2), u0 (LAST)
+    static constexpr int NC = 1 + (KM2 ? 1 : 0) + (LAST ? 1 : 0);
+    __device__ void apply_c(long long idx, A Au, A w, A dkm1, A c0, A c1, A c2) {
+        apply(idx, Au, w, dkm1, Pre{KM2 ? c1 : A(0), c0, LAST ? (KM2 ? c2 : c1) : A(0)});
+    }
+    __device__ void init() {}
+    __device__ bool skip() const { return false; }
+    __device__ Pre prefetch(long long idx) const {
+        return Pre{KM2 ? cvt<A>(ldg(dkm2 + idx)) : A(0), cvt<A>(ldg(y0 + idx)), LAST ? cvt<A>(u0[idx]) : A(0)};
+    }
+    __device__ void apply(long long idx, A Au, A w, A dkm1, const Pre& p) {
+        const A d = mu * dkm1 + nu * p.dkm2 + mdt * (w * Au) + ydt * p.y0;
+        out[idx] = cvt<S>(LAST ? p.u0 + d : d);
+    }
+    __device__ void finish() {}
+};
+
+// PCG set-up on the system S x = b, S = M - dt A, b = M u^n (the record's 4th word is M = 1/w):
+//   r = b - S x = M (u^n - x) + dt A x,  D^-1 = 1/(M - dt diag A),  and the sums <r, D^-1 r>,
+//   <r, r>, <b, b>; the last block initialises the scalar state.
+template <class P>
+struct EpiPcgInit {
+    using A = typename P::A;
+    using S = typename P::S;
+    using C = typename P::C;
+    struct Pre { A un, ad; };
+    const S* un;
+    S* r;
+    S* dinv;
+    const C* adiag;
+    PcgScalars* sc;
+    double* part;
+    unsigned int* counter;
+    int nblocks;
+    A dt;
+    double acc[3];
+    __device__ void init() { acc[0] = acc[1] = acc[2] = 0.0; }
+    __device__ bool skip() const { return false; }
+    __device__ Pre prefetch(long long idx) const { return Pre{cvt<A>(un[idx]), (A)__ldg(adiag + idx)}; }
+    __device__ void apply(long long idx, A Au, A m, A x, const Pre& p) {
+        const S rs = cvt<S>(m * (p.un - x) + dt * Au);
+        const S ds = cvt<S>(A(1) / (m - dt * p.ad));
+        r[idx] = rs;
+        dinv[idx] = ds;
+        const double rd = (double)cvt<A>(rs);
+        const double z = (double)cvt<A>(cvt<S>(cvt<A>(ds) * cvt<A>(rs)));
+        const double b = (double)(m * p.un);
+        acc[0] += rd * z;
+        acc[1] += rd * rd;
+        acc[2] += b * b;
+    }
+    __device__ void finish() {
+        block_sum<3>(acc);
+        const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+        if (tid == 0) {
+            part[blockIdx.x * 4 + 0] = acc[0];
+            part[blockIdx.x * 4 + 1] = acc[1];
+            part[blockIdx.x * 4 + 2] = acc[2];
+        }
+        if (last_block(counter, nblocks)) {
+            double v[3];
+            sum_partials<3>(part, nblocks, 4, v);
+            if (tid == 0) {
+                sc->rz = v[0];
+                sc->rr = v[1];
+                sc->bb = v[2];
+                sc->iter = 0;
+                sc->first = 1;
+                sc->beta = 0.0;
+                sc->alpha = 0.0;
+                const long long limit = sc->fixed > 0 ? sc->fixed : sc->max_iter;
+                int done = 0;
+                if (!(v[0] == v[0]) || !(v[1] == v[1]) || !(v[2] == v[2])) done = 2;
+                else if (sc->fixed == 0 && v[1] <= sc->tol2 * v[2]) done = 1;
+                else if (limit == 0) done = 3;
+                sc->done = done;
+                *counter = 0u;
+            }
+        }
+    }
+};
+
+// PCG SpMV: p (from the loader) is stored, q = S p = M p - dt A p, and <p, q> gives alpha.
+template <class P>
+struct EpiPcgSpmv {
+    using A = typename P::A;
+    using S = typename P::S;
+    using Pre = NoPre;
+    S* pout;
+    S* q;
+    PcgScalars* sc;
+    double* part;
+    unsigned int* counter;
+    int nblocks;
+    A dt;
+    int done;
+    double acc[1];
+    __device__ void init() {
+        acc[0] = 0.0;
+        done = sc->done;
+    }
+    __device__ bool skip() const { return done != 0; }
+    __device__ Pre prefetch(long long) const { return {}; }
+    __device__ void apply(long long idx, A Au, A m, A pv, const Pre&) {
+        const S ps = cvt<S>(pv);
+        const S qs = cvt<S>(m * pv - dt * Au);
+        pout[idx] = ps;
+        q[idx] = qs;
+        acc[0] += (double)cvt<A>(ps) * (double)cvt<A>(qs);
+    }
+    __device__ void finish() {
+        block_sum<1>(acc);
+        const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+        if (tid == 0) part[blockIdx.x * 4] = acc[0];
+        if (last_block(counter, nblocks)) {
+            double v[1];
+            sum_partials<1>(part, nblocks, 4, v);
+            if (tid == 0) {
+                const double pq = v[0];
+                sc->pq = pq;
+                if (!(pq > 0.0) || !(pq <= 1.79769313486231570e308)) sc->done = 2;
+                else sc->alpha = sc->rz / pq;
+                *counter = 0u;
+            }
+        }
+    }
+};
+
+// ---- element-wise kernels ------------------------------------------------------------------
+// d1 = a y0 (STS stage-1 increment when the cycle length is known only after the PTL pass).
+template <class P>
+__global__ void stage1_kernel(long long n, const typename P::S* y0, typename P::S* d1, typename P::A a) {
+    using A = typename P::A;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        d1[t] = cvt<typename P::S>(a * cvt<A>(y0[t]));
+}
+
+// PCG update: x += alpha p, r -= alpha q, z = D^-1 r, sums <r, z> and <r, r>; the last block
+// applies the stopping test (r.r <= rtol^2 b.b after the update) and forms beta.
+template <class P>
+__global__ void __launch_bounds__(256)
+pcg_update_kernel(long long n, typename P::S* x, typename P::S* r, const typename P::S* p,
+                  const typename P::S* q, const typename P::S* dinv, PcgScalars* sc,
+                  double* part, unsigned int* counter) {
+    using A = typename P::A;
+    using S = typename P::S;
+    if (sc->done) return;
+    const A alpha = (A)sc->alpha;
+    double acc[2] = {0.0, 0.0};
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        x[t] = cvt<S>(cvt<A>(x[t]) + alpha * cvt<A>(p[t]));
+        const S rs = cvt<S>(cvt<A>(r[t]) - alpha * cvt<A>(q[t]));
+        r[t] = rs;
+        const A ra = cvt<A>(rs);
+        const double z = (double)cvt<A>(cvt<S>(cvt<A>(dinv[t]) * ra));
+        acc[0] += (double)ra * z;
+        acc[1] += (double)ra * (double)ra;
+    }
+    block_sum<2>(acc);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x * 4 + 0] = acc[0];
+        part[blockIdx.x * 4 + 1] = acc[1];
+    }
+    if (last_block(counter, gridDim.x)) {
+        double v[2];
+        sum_partials<2>(part, gridDim.x, 4, v);
+        if (threadIdx.x == 0) {
+            const double rz = v[0], rr = v[1];
+            sc->rr = rr;
+            sc->iter += 1;
+            int done = 0;
+            if (!(rr == rr) || !(rz == rz)) done = 2;
+            else if (sc->fixed > 0) done = sc->iter >= sc->fixed ? 1 : 0;
+            else if (rr <= sc->tol2 * sc->bb) done = 1;
+            else if (sc->iter >= sc->max_iter) done = 3;
+            if (!done) {
+                sc->beta = rz / sc->rz;
+                sc->rz = rz;
+                sc->first = 0;
+            }
+            sc->done = done;
+            *counter = 0u;
+        }
+    }
+}
+
+// PTL (Eq. 5) at k = argmax |F| over the block partials; one block.
+template <class P>
+__global__ void __launch_bounds__(256)
+ptl_finalize_kernel(MarchGrid g, const typename P::S* u, const typename P::S* F,
+                    const ArgMax* part, int nparts, PtlResult* res, const int* nonfinite) {
+    using A = typename P::A;
+    double v = -1.0;
+    long long i = LLONG_MAX;
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+        const ArgMax m = part[b];
+        argmax_merge(v, i, m.v, m.i);
+    }
+    block_argmax(v, i);
+    if (threadIdx.x != 0) return;
+    PtlResult out;
+    out.nonfinite = *nonfinite;
+    out.fmax = v;
+    out.k = i;
+    out.dt_ptl = 1.0 / 0.0;
+    out.pad = 0;
+    if (i >= 0 && i != LLONG_MAX) {
+        int comp = 0;
+        for (int c = 1; c < g.ncomp; ++c)
+            if (i >= g.c[c].offset) comp = c;
+        const CompGrid& cg = g.c[comp];
+        const long long loc = i - cg.offset;
+        const long long plane = (long long)cg.nr * cg.nt;
+        const int kk = (int)(loc / plane);
+        const long long rem = loc - (long long)kk * plane;
+        const int jj = (int)(rem / cg.nr);
+        const int ii = (int)(rem - (long long)jj * cg.nr);
+        long long nb[6];
+        int nn = 0;
+        if (ii > 0) nb[nn++] = i - 1;
+        if (ii < cg.nr - 1) nb[nn++] = i + 1;
+        if (jj > 0) nb[nn++] = i - cg.nr;
+        if (jj < cg.nt - 1) nb[nn++] = i + cg.nr;
+        nb[nn++] = cg.offset + (long long)((kk + cg.np - 1) % cg.np) * plane + rem;
+        nb[nn++] = cg.offset + (long long)((kk + 1) % cg.np) * plane + rem;
+        const double uk = (double)cvt<A>(u[i]), fk = (double)cvt<A>(F[i]);
+        double best = 1.0 / 0.0;
+        for (int a = 0; a < nn; ++a) {
+            const double du = uk - (double)cvt<A>(u[nb[a]]);
+            const double df = fk - (double)cvt<A>(F[nb[a]]);
+            if (du != 0.0 && df != 0.0 && du * df < 0.0) best = fmin(best, -du / df);
+        }
+        out.dt_ptl = best;
+    }
+    *res = out;
+}
+
+}  // namespace pb

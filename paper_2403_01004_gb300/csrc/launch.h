@@ -1,0 +1,47 @@
+// Host-side kernel launchers, one implementation per precision policy (see ops_*.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace pb {
+
+// d_k = mu d_{k-1} + nu d_{k-2} + mdt F(d_{k-1}) + ydt y0   (increment form, see EpiStage)
+struct StageCoef { double mu, nu, mdt, ydt; };
+
+class Ops {
+public:
+    virtual ~Ops() {}
+    // F = L u over the whole state
+    virtual void apply(Ctx& c, const void* u, void* F) = 0;
+    // y0 = L u, with the PTL arg-max partials (argmax = true) or the fused stage-1 increment
+    // d1 = a y0 (d1 != nullptr)
+    virtual void y0_pass(Ctx& c, const void* u, void* y0, bool argmax, void* d1, double a) = 0;
+    // Eq. 5 at argmax |F|; result in c.d_ptl
+    virtual void ptl_finalize(Ctx& c, const void* u, const void* F) = 0;
+    // d1 = a y0
+    virtual void stage1(Ctx& c, const void* y0, void* d1, double a) = 0;
+    // one STS stage k >= 2 on increments; dkm2 == nullptr means d_{k-2} = 0 (k = 2); u0 !=
+    // nullptr marks the last stage, which writes u0 + d_s into out
+    virtual void stage(Ctx& c, const void* dkm1, const void* dkm2, const void* u0, const void* y0,
+                       void* out, const StageCoef& k) = 0;
+    // PCG: set-up from x (in place) and u^n; one SpMV + update iteration
+    virtual void pcg_init(Ctx& c, const void* x, const void* un, double dt) = 0;
+    virtual void pcg_iter(Ctx& c, void* x, int parity, double dt) = 0;
+    // converts the float64 coefficient records into the context's storage precision
+    virtual void store_coefs(Ctx& c, const Coef4<double>* rec, const double* adiag) = 0;
+    virtual bool supports_pcg() const = 0;
+};
+
+Ops* ops_f64();
+Ops* ops_f32();
+Ops* ops_b16();
+
+// set-up kernels (float64), see setup.cu
+void setup_tc(Ctx& c, const pb_grid& g, const pb_operator& op, Coef4<double>* rec, double* adiag,
+              double* dt_e);
+void setup_visc(Ctx& c, const pb_grid& g, const pb_operator& op, Coef4<double>* rec, double* adiag,
+                double* dt_e);
+
+int reduce_blocks(const Ctx& c);   // grid size of the element-wise reduction kernels
+
+}  // namespace pb

@@ -1,0 +1,274 @@
+// The two flux-form stencils (Eq. 2), written as phi-marching tile kernels.
+//
+// A block owns a TX x TY tile of (r, theta) points and walks a chunk of consecutive phi planes.
+// Per plane it stages the input field (with a one-point halo) in shared memory, forms the
+// stencil A u for its points and hands (A u, w, u_center) to an epilogue that fuses whatever
+// the caller needs (an STS stage update, y0 = F(u) with the PTL arg-max, a PCG SpMV, ...).
+// The input field comes from a loader, so fused element-wise producers (p = z + beta p in PCG)
+// are evaluated on the fly for the halo as well.
+//
+// Conduction (27-point corner scheme).  Corner c = (i+1/2, j+1/2, k+1/2) carries the record
+// ahat_c; its field-aligned gradient is s_c = ahat_c . D_c with D_c,x the sum of the four cell
+// differences straddling c along x, and its flux Q_c = ahat_c s_c.  A cell at position
+// p in {0,1}^3 inside corner c receives -sigma(p) . Q_c, sigma = 2p - 1.  Writing
+//   E0 = Qr+Qt+Qp, E1 = Qr+Qt-Qp, E2 = Qr-Qt+Qp, E3 = Qr-Qt-Qp
+// per corner, the eight corner contributions of cell (i,j,k) are
+//   (A u) = -[E0(i-1,j-1,k-1) - E0(i,j,k) + E1(i-1,j-1,k) - E1(i,j,k-1)
+//             + E2(i-1,j,k-1) - E2(i,j-1,k) + E3(i-1,j,k) - E3(i,j-1,k-1)].
+// Corners outside the interior carry ahat = 0 (zero-flux boundaries).
+//
+// Viscosity (7-point): (A u)_i = sum over the six faces of c_f (u_nbr - u_i), the record of
+// point i holding the coefficients of its +r, +theta, +phi faces.
+#pragma once
+
+#include "common.cuh"
+#include "reduce.cuh"
+
+namespace pb {
+
+__device__ __forceinline__ int wrap_phi(int k, int np) {
+    k %= np;
+    return k < 0 ? k + np : k;
+}
+
+// Decodes blockIdx.x into (component, tile origin, phi chunk).
+struct TileIdx { int comp, i0, j0, k0, k1; };
+
+__device__ __forceinline__ TileIdx decode_tile(const MarchGrid& g) {
+    int b = blockIdx.x;
+    int comp = 0;
+    if (g.ncomp > 1 && b >= g.c[1].block_begin) comp = 1;
+    if (g.ncomp > 2 && b >= g.c[2].block_begin) comp = 2;
+    const CompGrid& c = g.c[comp];
+    b -= c.block_begin;
+    const int tr = b % c.tiles_r; b /= c.tiles_r;
+    const int tt = b % c.tiles_t;
+    const int ch = b / c.tiles_t;
+    TileIdx t;
+    t.comp = comp;
+    t.i0 = tr * TX;
+    t.j0 = tt * TY;
+    t.k0 = ch * c.kchunk;
+    t.k1 = min(t.k0 + c.kchunk, c.np);
+    return t;
+}
+
+template <typename A> struct Quad { A e0, e1, e2, e3; };
+
+// ---------------------------------------------------------------------------------------------
+// Conduction march kernel.
+// Loader: A operator()(long long idx) const   (idx valid);   void init();
+// Epi: init(), skip(), Pre prefetch(idx), apply(idx, Au, w, center, pre), finish()
+// ---------------------------------------------------------------------------------------------
+template <class P, class Load, class Epi>
+__global__ void __launch_bounds__(NTHREADS)
+tc_march(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld_in, Epi ep_in) {
+    using A = typename P::A;
+    __shared__ A cell[2][TY + 2][TX + 2];
+    __shared__ Quad<A> corn[2][TY + 1][TX + 1];
+
+    Epi ep = ep_in;
+    ep.init();
+    if (ep.skip()) return;
+    Load ld = ld_in;
+    ld.init();
+
+    const TileIdx t = decode_tile(g);
+    const CompGrid& cg = g.c[0];
+    const int nr = cg.nr, nt = cg.nt, np = cg.np;
+    const long long plane = (long long)nr * nt;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+    const int i = t.i0 + tx, j = t.j0 + ty;
+    const bool own = (i < nr) && (j < nt);
+
+    // halo slot handled by thread `tid` (84 halo cells for a 32 x 8 tile)
+    int hi = -1, hj = -1;
+    if (tid < 2 * (TX + 2)) {
+        hi = tid % (TX + 2);
+        hj = tid < TX + 2 ? 0 : TY + 1;
+    } else if (tid < 2 * (TX + 2) + 2 * TY) {
+        const int q = tid - 2 * (TX + 2);
+        hi = q < TY ? 0 : TX + 1;
+        hj = 1 + (q % TY);
+    }
+    // extra corner handled by thread `tid` (41 corners on the low-r / low-theta edges)
+    int xci = -1, xcj = -1;
+    if (tid < TY + 1) { xci = 0; xcj = tid; }
+    else if (tid < TY + 1 + TX) { xci = tid - TY; xcj = 0; }
+
+    auto fetch = [&](int gi, int gj, int kk) -> A {
+        if (gi < 0 || gi >= nr || gj < 0 || gj >= nt) return A(0);
+        return ld(cg.offset + (long long)wrap_phi(kk, np) * plane + (long long)gj * nr + gi);
+    };
+    auto fetch_coef = [&](int ci, int cj, int kk) -> Coef4<A> {
+        const int gi = t.i0 - 1 + ci, gj = t.j0 - 1 + cj;
+        if (gi < 0 || gi >= nr || gj < 0 || gj >= nt) return Coef4<A>{A(0), A(0), A(0), A(0)};
+        return load_coef<A, typename P::C>(coef + cg.offset + (long long)wrap_phi(kk, np) * plane + (long long)gj * nr + gi);
+    };
+    // Corner (ci, cj) of the (TX+1) x (TY+1) corner grid from cell planes `pa` (k) and `pb` (k+1).
+    auto corner = [&](int cbuf, int pa, int pb, int ci, int cj, const Coef4<A>& c) {
+        const A u000 = cell[pa][cj][ci], u100 = cell[pa][cj][ci + 1];
+        const A u010 = cell[pa][cj + 1][ci], u110 = cell[pa][cj + 1][ci + 1];
+        const A u001 = cell[pb][cj][ci], u101 = cell[pb][cj][ci + 1];
+        const A u011 = cell[pb][cj + 1][ci], u111 = cell[pb][cj + 1][ci + 1];
+        const A P00 = u001 + u000, M00 = u001 - u000;
+        const A P10 = u101 + u100, M10 = u101 - u100;
+        const A P01 = u011 + u010, M01 = u011 - u010;
+        const A P11 = u111 + u110, M11 = u111 - u110;
+        const A X = P11 - P00, Y = P10 - P01;
+        const A Dr = X + Y, Dt = X - Y, Dp = (M00 + M01) + (M10 + M11);
+        const A s = c.a * Dr + c.b * Dt + c.c * Dp;
+        const A Qr = c.a * s, Qt = c.b * s, Qp = c.c * s;
+        const A t1 = Qr + Qt, t2 = Qr - Qt;
+        corn[cbuf][cj][ci] = Quad<A>{t1 + Qp, t1 - Qp, t2 + Qp, t2 - Qp};
+    };
+
+    // prologue: cell planes k0-1, k0 and corner plane k0-1 into shared memory
+    cell[0][ty + 1][tx + 1] = fetch(i, j, t.k0 - 1);
+    if (hi >= 0) cell[0][hj][hi] = fetch(t.i0 - 1 + hi, t.j0 - 1 + hj, t.k0 - 1);
+    cell[1][ty + 1][tx + 1] = fetch(i, j, t.k0);
+    if (hi >= 0) cell[1][hj][hi] = fetch(t.i0 - 1 + hi, t.j0 - 1 + hj, t.k0);
+    {
+        const Coef4<A> c0 = fetch_coef(tx + 1, ty + 1, t.k0 - 1);
+        Coef4<A> c1{A(0), A(0), A(0), A(0)};
+        if (xci >= 0) c1 = fetch_coef(xci, xcj, t.k0 - 1);
+        __syncthreads();
+        corner(0, 0, 1, tx + 1, ty + 1, c0);
+        if (xci >= 0) corner(0, 0, 1, xci, xcj, c1);
+    }
+    // register prefetch of the next plane: cell plane k+1, corner records of plane k, epilogue
+    // operands of plane k
+    A nu_own = fetch(i, j, t.k0 + 1);
+    A nu_halo = hi >= 0 ? fetch(t.i0 - 1 + hi, t.j0 - 1 + hj, t.k0 + 1) : A(0);
+    Coef4<A> nc_own = fetch_coef(tx + 1, ty + 1, t.k0);
+    Coef4<A> nc_x{A(0), A(0), A(0), A(0)};
+    if (xci >= 0) nc_x = fetch_coef(xci, xcj, t.k0);
+    typename Epi::Pre npre{};
+    if (own) npre = ep.prefetch(cg.offset + (long long)t.k0 * plane + (long long)j * nr + i);
+    __syncthreads();
+
+    int cb = 1;   // cell buffer holding plane k
+    int kb = 0;   // corner buffer holding corner plane k-1
+    for (int k = t.k0; k < t.k1; ++k) {
+        const long long idx = cg.offset + (long long)k * plane + (long long)j * nr + i;
+        cell[cb ^ 1][ty + 1][tx + 1] = nu_own;
+        if (hi >= 0) cell[cb ^ 1][hj][hi] = nu_halo;
+        const Coef4<A> c_own = nc_own, c_x = nc_x;
+        const typename Epi::Pre pre = npre;
+        if (k + 1 < t.k1) {
+            nu_own = fetch(i, j, k + 2);
+            if (hi >= 0) nu_halo = fetch(t.i0 - 1 + hi, t.j0 - 1 + hj, k + 2);
+            nc_own = fetch_coef(tx + 1, ty + 1, k + 1);
+            if (xci >= 0) nc_x = fetch_coef(xci, xcj, k + 1);
+            if (own) npre = ep.prefetch(idx + plane);
+        }
+        __syncthreads();
+        corner(kb ^ 1, cb, cb ^ 1, tx + 1, ty + 1, c_own);
+        if (xci >= 0) corner(kb ^ 1, cb, cb ^ 1, xci, xcj, c_x);
+        const A center = cell[cb][ty + 1][tx + 1];
+        __syncthreads();
+        if (own) {
+            const Quad<A>(&Cp)[TY + 1][TX + 1] = corn[kb];       // corner plane k-1
+            const Quad<A>(&Cc)[TY + 1][TX + 1] = corn[kb ^ 1];   // corner plane k
+            const A sum = (Cp[ty][tx].e0 - Cc[ty + 1][tx + 1].e0) + (Cc[ty][tx].e1 - Cp[ty + 1][tx + 1].e1)
+                        + (Cp[ty + 1][tx].e2 - Cc[ty][tx + 1].e2) + (Cc[ty + 1][tx].e3 - Cp[ty][tx + 1].e3);
+            ep.apply(idx, -sum, c_own.w, center, pre);
+        }
+        cb ^= 1;
+        kb ^= 1;
+    }
+    ep.finish();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Viscosity march kernel (all three components in one launch).
+// ---------------------------------------------------------------------------------------------
+template <class P, class Load, class Epi>
+__global__ void __launch_bounds__(NTHREADS)
+visc_march(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld_in, Epi ep_in) {
+    using A = typename P::A;
+    using C = typename P::C;
+    __shared__ A us[TY + 2][TX + 2];
+    __shared__ A crs[TY][TX + 1];
+    __shared__ A cts[TY + 1][TX];
+
+    Epi ep = ep_in;
+    ep.init();
+    if (ep.skip()) return;
+    Load ld = ld_in;
+    ld.init();
+
+    const TileIdx t = decode_tile(g);
+    const CompGrid& cg = g.c[t.comp];
+    const int nr = cg.nr, nt = cg.nt, np = cg.np;
+    const long long plane = (long long)nr * nt;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = t.i0 + tx, j = t.j0 + ty;
+    const bool own = (i < nr) && (j < nt);
+
+    auto gidx = [&](int gi, int gj, int kk) -> long long {
+        return cg.offset + (long long)wrap_phi(kk, np) * plane + (long long)gj * nr + gi;
+    };
+    auto fetch = [&](int gi, int gj, int kk) -> A {
+        if (gi < 0 || gi >= nr || gj < 0 || gj >= nt) return A(0);
+        return ld(gidx(gi, gj, kk));
+    };
+    auto fetch_coef = [&](int gi, int gj, int kk) -> Coef4<A> {
+        if (gi < 0 || gi >= nr || gj < 0 || gj >= nt) return Coef4<A>{A(0), A(0), A(0), A(0)};
+        return load_coef<A, C>(coef + gidx(gi, gj, kk));
+    };
+
+    // registers: u of this point at planes k-1, k, k+1; its -phi face coefficient; and a
+    // one-plane prefetch of everything plane k+1 needs
+    A ukm = fetch(i, j, t.k0 - 1);
+    A uk = fetch(i, j, t.k0);
+    A ukp = fetch(i, j, t.k0 + 1);
+    A cpm = fetch_coef(i, j, t.k0 - 1).c;
+    Coef4<A> nc = fetch_coef(i, j, t.k0);
+    A n_ul = tx == 0 ? fetch(i - 1, j, t.k0) : A(0);
+    A n_ur = tx == TX - 1 ? fetch(i + 1, j, t.k0) : A(0);
+    A n_ub = ty == 0 ? fetch(i, j - 1, t.k0) : A(0);
+    A n_ut = ty == TY - 1 ? fetch(i, j + 1, t.k0) : A(0);
+    A n_crl = tx == 0 ? fetch_coef(i - 1, j, t.k0).a : A(0);
+    A n_ctb = ty == 0 ? fetch_coef(i, j - 1, t.k0).b : A(0);
+    typename Epi::Pre npre{};
+    if (own) npre = ep.prefetch(gidx(i, j, t.k0));
+
+    for (int k = t.k0; k < t.k1; ++k) {
+        const long long idx = gidx(i, j, k);
+        const Coef4<A> c = nc;
+        const typename Epi::Pre pre = npre;
+        us[ty + 1][tx + 1] = uk;
+        crs[ty][tx + 1] = c.a;
+        cts[ty + 1][tx] = c.b;
+        if (tx == 0) { us[ty + 1][0] = n_ul; crs[ty][0] = n_crl; }
+        if (tx == TX - 1) us[ty + 1][TX + 1] = n_ur;
+        if (ty == 0) { us[0][tx + 1] = n_ub; cts[0][tx] = n_ctb; }
+        if (ty == TY - 1) us[TY + 1][tx + 1] = n_ut;
+        A ukpp = A(0);
+        if (k + 1 < t.k1) {
+            ukpp = fetch(i, j, k + 2);
+            nc = fetch_coef(i, j, k + 1);
+            if (tx == 0) { n_ul = fetch(i - 1, j, k + 1); n_crl = fetch_coef(i - 1, j, k + 1).a; }
+            if (tx == TX - 1) n_ur = fetch(i + 1, j, k + 1);
+            if (ty == 0) { n_ub = fetch(i, j - 1, k + 1); n_ctb = fetch_coef(i, j - 1, k + 1).b; }
+            if (ty == TY - 1) n_ut = fetch(i, j + 1, k + 1);
+            if (own) npre = ep.prefetch(gidx(i, j, k + 1));
+        }
+        __syncthreads();
+        if (own) {
+            const A Au = crs[ty][tx + 1] * (us[ty + 1][tx + 2] - uk) + crs[ty][tx] * (us[ty + 1][tx] - uk)
+                       + cts[ty + 1][tx] * (us[ty + 2][tx + 1] - uk) + cts[ty][tx] * (us[ty][tx + 1] - uk)
+                       + c.c * (ukp - uk) + cpm * (ukm - uk);
+            ep.apply(idx, Au, c.w, uk, pre);
+        }
+        __syncthreads();
+        ukm = uk;
+        uk = ukp;
+        ukp = ukpp;
+        cpm = c.c;
+    }
+    ep.finish();
+}
+
+}  // namespace pb

@@ -1,0 +1,184 @@
+// Conduction march kernel with a TMA pipeline (the production path on sm_103a).
+//
+// Same stencil and epilogues as tc_march (march.cuh), but every global operand of a phi plane --
+// the input field with its halo, the corner records and the epilogue's point operands -- arrives
+// by cp.async.bulk.tensor into a ring of D shared-memory slots, tracked by one mbarrier per slot.
+// One elected thread keeps D-1 planes of loads in flight; out-of-range halo points (r_min,
+// r_max, the poles) come back as zeros from the TMA bounds handling, and phi wraps by issuing
+// the wrapped plane index.  The x (r) box origin is rounded down by HX points so that its byte
+// offset is 16-byte aligned.
+//
+// Slot q of a block holds plane k0 - 1 + q; iteration k (plane k) needs slots k-k0+1 (plane k:
+// field, corners k+1/2, point operands) and k-k0+2 (plane k+1: field).  Every wait is bounded:
+// if a copy never lands the block records the failure in *err, waits (bounded) for its other
+// copies and returns.
+#pragma once
+
+#include "march.cuh"
+#include "tma.cuh"
+
+namespace pb {
+
+template <typename S> struct HaloPad { static constexpr int value = 16 / (int)sizeof(S); };
+
+constexpr int kSlots = 4;
+
+__host__ __device__ constexpr int align128(int b) { return (b + 127) & ~127; }
+
+template <class P, int NC>
+struct TmaLayout {
+    using S = typename P::S;
+    using C = typename P::C;
+    using A = typename P::A;
+    static constexpr int HX = HaloPad<S>::value;
+    static constexpr int BXW = TX + 2 * HX;                              // halo box width (points)
+    static constexpr int U_BYTES = (TY + 2) * BXW * (int)sizeof(S);
+    static constexpr int C_BYTES = (TY + 1) * (TX + 1) * 4 * (int)sizeof(C);
+    static constexpr int E_BYTES = TY * TX * (int)sizeof(S);
+    static constexpr int U_OFF = 0;
+    static constexpr int C_OFF = align128(U_BYTES);
+    static constexpr int E_OFF = C_OFF + align128(C_BYTES);
+    static constexpr int SLOT = E_OFF + NC * align128(E_BYTES);
+    static constexpr int TX_BYTES = U_BYTES + C_BYTES + NC * E_BYTES;    // bytes a slot's copies deliver
+    static constexpr int CW = TX + 2;                                    // corner row pitch
+    static constexpr int CORN_OFF = kSlots * SLOT;
+    static constexpr int CORN_BYTES = 2 * 4 * (TY + 1) * CW * (int)sizeof(A);
+    static constexpr int BAR_OFF = align128(CORN_OFF + CORN_BYTES);
+    static constexpr int TOTAL = BAR_OFF + kSlots * 8 + 16;
+};
+
+template <class P, class Epi>
+__global__ void __launch_bounds__(NTHREADS)
+tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* err) {
+    using S = typename P::S;
+    using C = typename P::C;
+    using A = typename P::A;
+    using L = TmaLayout<P, Epi::NC>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // TMA destinations are kept 128-byte aligned (the launch adds 128 bytes of slack)
+    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
+    int* abort_flag = reinterpret_cast<int*>(smem + L::BAR_OFF + kSlots * 8);
+    A* corn = reinterpret_cast<A*>(smem + L::CORN_OFF);
+
+    Epi ep = ep_in;
+    ep.init();
+    if (ep.skip()) return;
+
+    const TileIdx t = decode_tile(g);
+    const CompGrid& cg = g.c[0];
+    const int nr = cg.nr, nt = cg.nt, np = cg.np;
+    const long long plane = (long long)nr * nt;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+    const int i = t.i0 + tx, j = t.j0 + ty;
+    const bool own = (i < nr) && (j < nt);
+    const int nplanes = t.k1 - t.k0 + 2;       // planes k0-1 .. k1
+
+    int xci = -1, xcj = -1;                    // extra corner of this thread (low-r / low-theta edge)
+    if (tid < TY + 1) { xci = 0; xcj = tid; }
+    else if (tid < TY + 1 + TX) { xci = tid - TY; xcj = 0; }
+
+    auto slot = [&](int q) -> unsigned char* { return smem + (q % kSlots) * L::SLOT; };
+    auto issue = [&](int q) {
+        unsigned char* s = slot(q);
+        uint64_t* bar = bars + (q % kSlots);
+        int z = t.k0 - 1 + q;
+        z = z < 0 ? z + np : (z >= np ? z - np : z);
+        mbar_expect_tx(bar, L::TX_BYTES);
+        tma_load_3d(s + L::U_OFF, &maps.halo, t.i0 - L::HX, t.j0 - 1, z, bar);
+        tma_load_4d(s + L::C_OFF, &maps.coef, 0, t.i0 - 1, t.j0 - 1, z, bar);
+#pragma unroll
+        for (int a = 0; a < Epi::NC; ++a) tma_load_3d(s + L::E_OFF + a * align128(L::E_BYTES), &maps.cen[a], t.i0, t.j0, z, bar);
+    };
+    // all threads wait for slot q; returns false (in every thread) if the copy never landed
+    auto wait = [&](int q) -> bool {
+        if (!mbar_wait(bars + (q % kSlots), (q / kSlots) & 1)) *abort_flag = 1;
+        __syncthreads();
+        return *abort_flag == 0;
+    };
+    auto bail = [&](int issued, int waited) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            for (int q = waited; q < issued; ++q) mbar_wait(bars + (q % kSlots), (q / kSlots) & 1);
+        }
+        __syncthreads();
+    };
+    auto U = [&](int q, int yy, int xx) -> A {
+        return cvt<A>(reinterpret_cast<const S*>(slot(q) + L::U_OFF)[yy * L::BXW + xx]);
+    };
+    // corner (ci, cj) of plane z = k0-1+q from field slots q (plane z) and q+1 (plane z+1)
+    auto corner = [&](int cbuf, int q, int ci, int cj) -> A {
+        const C* cr = reinterpret_cast<const C*>(slot(q) + L::C_OFF) + 4 * (cj * (TX + 1) + ci);
+        const A ca = (A)cr[0], cb = (A)cr[1], cc = (A)cr[2], cw = (A)cr[3];
+        const int x0 = ci - 1 + L::HX;
+        const A u000 = U(q, cj, x0), u100 = U(q, cj, x0 + 1);
+        const A u010 = U(q, cj + 1, x0), u110 = U(q, cj + 1, x0 + 1);
+        const A u001 = U(q + 1, cj, x0), u101 = U(q + 1, cj, x0 + 1);
+        const A u011 = U(q + 1, cj + 1, x0), u111 = U(q + 1, cj + 1, x0 + 1);
+        const A P00 = u001 + u000, M00 = u001 - u000;
+        const A P10 = u101 + u100, M10 = u101 - u100;
+        const A P01 = u011 + u010, M01 = u011 - u010;
+        const A P11 = u111 + u110, M11 = u111 - u110;
+        const A X = P11 - P00, Y = P10 - P01;
+        const A Dr = X + Y, Dt = X - Y, Dp = (M00 + M01) + (M10 + M11);
+        const A s = ca * Dr + cb * Dt + cc * Dp;
+        const A Qr = ca * s, Qt = cb * s, Qp = cc * s;
+        const A t1 = Qr + Qt, t2 = Qr - Qt;
+        A* cp = corn + cbuf * 4 * (TY + 1) * L::CW + cj * L::CW + ci;
+        cp[0 * (TY + 1) * L::CW] = t1 + Qp;
+        cp[1 * (TY + 1) * L::CW] = t1 - Qp;
+        cp[2 * (TY + 1) * L::CW] = t2 + Qp;
+        cp[3 * (TY + 1) * L::CW] = t2 - Qp;
+        return cw;
+    };
+    auto E = [&](int cbuf, int e, int cj, int ci) -> A {
+        return corn[cbuf * 4 * (TY + 1) * L::CW + e * (TY + 1) * L::CW + cj * L::CW + ci];
+    };
+
+    if (tid == 0) {
+        *abort_flag = 0;
+        for (int b = 0; b < kSlots; ++b) mbar_init(bars + b, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    int issued = 0;
+    if (tid == 0)
+        for (; issued < kSlots && issued < nplanes; ++issued) issue(issued);
+    issued = min(kSlots, nplanes);
+
+    // corner plane k0-1 from slots 0 and 1
+    if (!wait(0) || !wait(1)) { bail(issued, 0); return; }
+    corner(0, 0, tx + 1, ty + 1);
+    if (xci >= 0) corner(0, 0, xci, xcj);
+    __syncthreads();
+    if (tid == 0 && issued < nplanes) issue(issued);
+    if (issued < nplanes) ++issued;
+
+    int kb = 0;
+    for (int k = t.k0; k < t.k1; ++k) {
+        const int q = k - t.k0 + 1;
+        if (!wait(q + 1)) { bail(issued, q + 1); return; }
+        const A w = corner(kb ^ 1, q, tx + 1, ty + 1);
+        if (xci >= 0) corner(kb ^ 1, q, xci, xcj);
+        const A center = U(q, ty + 1, tx + L::HX);
+        auto cen = [&](int a) -> A {
+            return a < Epi::NC ? cvt<A>(reinterpret_cast<const S*>(slot(q) + L::E_OFF + a * align128(L::E_BYTES))[ty * TX + tx])
+                               : A(0);
+        };
+        const A c0 = cen(0), c1 = cen(1), c2 = cen(2);
+        __syncthreads();
+        // slot q is no longer read: refill it with plane k0-1+q+kSlots
+        if (tid == 0 && issued < nplanes) issue(issued);
+        if (issued < nplanes) ++issued;
+        if (own) {
+            const A sum = (E(kb, 0, ty, tx) - E(kb ^ 1, 0, ty + 1, tx + 1)) + (E(kb ^ 1, 1, ty, tx) - E(kb, 1, ty + 1, tx + 1))
+                        + (E(kb, 2, ty + 1, tx) - E(kb ^ 1, 2, ty, tx + 1)) + (E(kb ^ 1, 3, ty + 1, tx) - E(kb, 3, ty, tx + 1));
+            const long long idx = cg.offset + (long long)k * plane + (long long)j * nr + i;
+            ep.apply_c(idx, -sum, w, center, c0, c1, c2);
+        }
+        kb ^= 1;
+    }
+    ep.finish();
+}
+
+}  // namespace pb

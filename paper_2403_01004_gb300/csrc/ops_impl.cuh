@@ -1,0 +1,165 @@
+// Launchers for one precision policy P; included by ops_f64.cu / ops_f32.cu / ops_b16.cu.
+#pragma once
+
+#include "epilogues.cuh"
+#include "launch.h"
+#include "march.cuh"
+#include "march_tma.cuh"
+
+namespace pb {
+
+template <class P>
+class OpsImpl : public Ops {
+    using S = typename P::S;
+    using C = typename P::C;
+    using A = typename P::A;
+
+    template <class Load, class Epi>
+    static void march(Ctx& c, const void* coef, const Load& ld, const Epi& ep) {
+        dim3 block(TX, TY);
+        const Coef4<C>* cf = static_cast<const Coef4<C>*>(coef);
+        if (c.kind == PB_TC_ANISO)
+            tc_march<P, Load, Epi><<<c.grid.nblocks, block, 0, c.stream>>>(c.grid, cf, ld, ep);
+        else
+            visc_march<P, Load, Epi><<<c.grid.nblocks, block, 0, c.stream>>>(c.grid, cf, ld, ep);
+        PB_CUDA_TRY(cudaGetLastError());
+    }
+
+    // Conduction march on a plain state field through the TMA kernel when every array can be
+    // described by a tensor map; otherwise the register-prefetch kernel.
+    template <class Epi>
+    static void march_state(Ctx& c, const void* field, const void* const* cen, const Epi& ep) {
+        if (c.kind == PB_TC_ANISO && c.use_tma) {
+            using L = TmaLayout<P, Epi::NC>;
+            const CompGrid& g = c.grid.c[0];
+            TmaMaps maps;
+            bool ok = tma_state_map(&maps.halo, field, sizeof(S), g.nr, g.nt, g.np, L::BXW, TY + 2) &&
+                      tma_coef_map(&maps.coef, c.coef, sizeof(C), g.nr, g.nt, g.np, TX + 1, TY + 1);
+            for (int a = 0; ok && a < Epi::NC; ++a)
+                ok = tma_state_map(&maps.cen[a], cen[a], sizeof(S), g.nr, g.nt, g.np, TX, TY);
+            if (ok) {
+                static bool attr = false;
+                const int smem = L::TOTAL + 128;
+                if (!attr) {
+                    PB_CUDA_TRY(cudaFuncSetAttribute(tc_march_tma<P, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                    attr = true;
+                }
+                tc_march_tma<P, Epi><<<c.grid.nblocks, dim3(TX, TY), smem, c.stream>>>(c.grid, maps, ep, c.d_err);
+                PB_CUDA_TRY(cudaGetLastError());
+                return;
+            }
+        }
+        march(c, c.coef, LoadState<P>{static_cast<const S*>(field)}, ep);
+    }
+
+public:
+    bool supports_pcg() const override { return P::id != PB_BF16_STORE; }
+
+    void apply(Ctx& c, const void* u, void* F) override {
+        EpiF<P, false, false> ep{static_cast<S*>(F), nullptr, A(0), nullptr, nullptr};
+        march_state(c, u, nullptr, ep);
+    }
+
+    void y0_pass(Ctx& c, const void* u, void* y0, bool argmax, void* u1, double a) override {
+        ArgMax* part = static_cast<ArgMax*>(c.partials);
+        if (argmax) {
+            PB_CUDA_TRY(cudaMemsetAsync(c.d_flag, 0, sizeof(int), c.stream));
+            if (u1) {
+                EpiF<P, true, true> ep{static_cast<S*>(y0), static_cast<S*>(u1), (A)a, part, c.d_flag};
+                march_state(c, u, nullptr, ep);
+            } else {
+                EpiF<P, true, false> ep{static_cast<S*>(y0), nullptr, A(0), part, c.d_flag};
+                march_state(c, u, nullptr, ep);
+            }
+        } else if (u1) {
+            EpiF<P, false, true> ep{static_cast<S*>(y0), static_cast<S*>(u1), (A)a, nullptr, nullptr};
+            march_state(c, u, nullptr, ep);
+        } else {
+            apply(c, u, y0);
+        }
+    }
+
+    void ptl_finalize(Ctx& c, const void* u, const void* F) override {
+        ptl_finalize_kernel<P><<<1, 256, 0, c.stream>>>(c.grid, static_cast<const S*>(u), static_cast<const S*>(F),
+                                                        static_cast<const ArgMax*>(c.partials), c.grid.nblocks,
+                                                        c.d_ptl, c.d_flag);
+        PB_CUDA_TRY(cudaGetLastError());
+    }
+
+    void stage1(Ctx& c, const void* y0, void* d1, double a) override {
+        const int blocks = reduce_blocks(c);
+        stage1_kernel<P><<<blocks, 256, 0, c.stream>>>(c.n, static_cast<const S*>(y0), static_cast<S*>(d1), (A)a);
+        PB_CUDA_TRY(cudaGetLastError());
+    }
+
+    template <bool KM2, bool LAST>
+    void stage_t(Ctx& c, const void* dkm1, const void* dkm2, const void* u0, const void* y0, void* out,
+                 const StageCoef& k) {
+        EpiStage<P, KM2, LAST> ep{static_cast<const S*>(dkm2), static_cast<const S*>(y0), static_cast<const S*>(u0),
+                                  static_cast<S*>(out), (A)k.mu, (A)k.nu, (A)k.mdt, (A)k.ydt};
+        const void* cen[3];
+        int n = 0;
+        cen[n++] = y0;
+        if (KM2) cen[n++] = dkm2;
+        if (LAST) cen[n++] = u0;
+        march_state(c, dkm1, cen, ep);
+    }
+
+    void stage(Ctx& c, const void* dkm1, const void* dkm2, const void* u0, const void* y0, void* out,
+               const StageCoef& k) override {
+        if (dkm2) {
+            if (u0) stage_t<true, true>(c, dkm1, dkm2, u0, y0, out, k);
+            else stage_t<true, false>(c, dkm1, dkm2, u0, y0, out, k);
+        } else {
+            if (u0) stage_t<false, true>(c, dkm1, dkm2, u0, y0, out, k);
+            else stage_t<false, false>(c, dkm1, dkm2, u0, y0, out, k);
+        }
+    }
+
+    void pcg_init(Ctx& c, const void* x, const void* un, double dt) override {
+        EpiPcgInit<P> ep{static_cast<const S*>(un), static_cast<S*>(c.r), static_cast<S*>(c.dinv),
+                         static_cast<const C*>(c.adiag), c.d_pcg, static_cast<double*>(c.partials),
+                         c.counter, c.grid.nblocks, (A)dt};
+        march(c, c.coef_be, LoadState<P>{static_cast<const S*>(x)}, ep);
+    }
+
+    void pcg_iter(Ctx& c, void* x, int parity, double dt) override {
+        S* pold = static_cast<S*>(c.p[parity]);
+        S* pnew = static_cast<S*>(c.p[parity ^ 1]);
+        LoadPcgP<P> ld{static_cast<const S*>(c.r), static_cast<const S*>(c.dinv), pold, c.d_pcg, A(0), 0};
+        EpiPcgSpmv<P> ep{pnew, static_cast<S*>(c.q), c.d_pcg, static_cast<double*>(c.partials), c.counter,
+                         c.grid.nblocks, (A)dt};
+        march(c, c.coef_be, ld, ep);
+        const int blocks = reduce_blocks(c);
+        pcg_update_kernel<P><<<blocks, 256, 0, c.stream>>>(c.n, static_cast<S*>(x), static_cast<S*>(c.r), pnew,
+                                                           static_cast<const S*>(c.q), static_cast<const S*>(c.dinv),
+                                                           c.d_pcg, static_cast<double*>(c.partials), c.counter);
+        PB_CUDA_TRY(cudaGetLastError());
+    }
+
+    void store_coefs(Ctx& c, const Coef4<double>* rec, const double* adiag) override;
+};
+
+template <class P>
+__global__ void store_coefs_kernel(long long n, const Coef4<double>* rec, const double* adiag,
+                                   Coef4<typename P::C>* out, Coef4<typename P::C>* out_be,
+                                   typename P::C* adiag_out) {
+    using C = typename P::C;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const Coef4<double> r = rec[t];
+        out[t] = Coef4<C>{(C)r.a, (C)r.b, (C)r.c, (C)r.w};
+        // the Backward Euler record carries the mass M = 1/w instead of w
+        out_be[t] = Coef4<C>{(C)r.a, (C)r.b, (C)r.c, (C)(1.0 / r.w)};
+        adiag_out[t] = (C)adiag[t];
+    }
+}
+
+template <class P>
+void OpsImpl<P>::store_coefs(Ctx& c, const Coef4<double>* rec, const double* adiag) {
+    store_coefs_kernel<P><<<reduce_blocks(c), 256, 0, c.stream>>>(c.n, rec, adiag, static_cast<Coef4<C>*>(c.coef),
+                                                                  static_cast<Coef4<C>*>(c.coef_be),
+                                                                  static_cast<C*>(c.adiag));
+    PB_CUDA_TRY(cudaGetLastError());
+}
+
+}  // namespace pb
