@@ -141,6 +141,12 @@ PB_API const char* pb_last_error(const pb_ctx* ctx);
 PB_API int parabolic_setup(const pb_grid* grid, const pb_operator* op, int32_t precision,
                     void* cuda_stream, pb_ctx** out);
 
+/* Recomputes the frozen coefficients and dt_E for new operator inputs (same kind and grid; for
+ * conduction a new lagged T0, density or field), in place: allocates nothing, runs on the
+ * context's stream, returns when done.  This is the once-per-step set-up of Sec. 2 (lagged
+ * diffusivity: kappa frozen at the previous step's temperature). */
+PB_API int parabolic_update(pb_ctx* ctx, const pb_operator* op);
+
 /* Frees the context and its device workspace.  NULL is accepted. */
 PB_API int parabolic_destroy(pb_ctx* ctx);
 
@@ -169,6 +175,26 @@ PB_API int rkl2_advance(pb_ctx* ctx, void* u_dev, double dt, const pb_advance_op
  * PB_FP64 and PB_FP32 (float vectors, float64 dot products).  stats may be NULL. */
 PB_API int be_pcg_advance(pb_ctx* ctx, void* u_dev, double dt, const pb_advance_opts* opts,
                    const void* x0_dev, pb_stats* stats);
+
+/* ---- kernel accounting --------------------------------------------------------------------- */
+/* Per kernel class of one context: launches, launches timed with CUDA events on the context's
+ * stream, their summed duration, and the algorithmic bytes the launches must move (every operand
+ * read once and every result written once; the per-point figures are in the library's design
+ * notes).  Launch counts are always kept. */
+typedef struct {
+    char name[32];            /* "<tc|visc>.<class>", e.g. "tc.stage", "visc.ptl_pass"        */
+    int64_t launches;
+    int64_t timed_launches;
+    double total_ms;
+    double bytes;
+} pb_kernel_stat;
+
+/* Resets the counters; on != 0 also brackets every launch with CUDA events (harvested at the
+ * library's host synchronisations) until called again with on = 0. */
+PB_API int pb_profile_enable(pb_ctx* ctx, int32_t on);
+
+/* Writes up to cap records (classes with at least one launch) and their number to *count. */
+PB_API int pb_profile_read(pb_ctx* ctx, pb_kernel_stat* out, int32_t cap, int32_t* count);
 
 #ifdef __cplusplus
 }

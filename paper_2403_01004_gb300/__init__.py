@@ -27,8 +27,8 @@ C_TC = (5.0 / 3.0 - 1.0) / 2.0
 
 # C function names exported by the library (kept in step with include/parabolic.h)
 EXPORTS = ("pb_advance_opts_init", "pb_status_string", "pb_last_error", "parabolic_setup",
-           "parabolic_destroy", "parabolic_state_size", "parabolic_dt_explicit", "parabolic_apply",
-           "ptl_compute", "rkl2_advance", "be_pcg_advance")
+           "parabolic_update", "parabolic_destroy", "parabolic_state_size", "parabolic_dt_explicit", "parabolic_apply",
+           "ptl_compute", "rkl2_advance", "be_pcg_advance", "pb_profile_enable", "pb_profile_read")
 
 
 class PbGrid(ctypes.Structure):
@@ -57,6 +57,11 @@ class PbStats(ctypes.Structure):
                 ("k_cycle", POINTER(c_int64))]
 
 
+class PbKernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", c_int64), ("timed_launches", c_int64),
+                ("total_ms", c_double), ("bytes", c_double)]
+
+
 class ParabolicError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"[{status}] {message}")
@@ -81,6 +86,7 @@ def load_library(path: str = LIB_PATH):
     lib.pb_last_error.argtypes = [c_void_p]
     lib.pb_last_error.restype = ctypes.c_char_p
     lib.parabolic_setup.argtypes = [POINTER(PbGrid), POINTER(PbOperator), c_int32, c_void_p, POINTER(c_void_p)]
+    lib.parabolic_update.argtypes = [c_void_p, POINTER(PbOperator)]
     lib.parabolic_destroy.argtypes = [c_void_p]
     lib.parabolic_state_size.argtypes = [c_void_p, POINTER(c_int64), POINTER(c_int32)]
     lib.parabolic_dt_explicit.argtypes = [c_void_p, POINTER(c_double)]
@@ -88,7 +94,9 @@ def load_library(path: str = LIB_PATH):
     lib.ptl_compute.argtypes = [c_void_p, c_void_p, POINTER(c_double), POINTER(c_int64), POINTER(c_double)]
     lib.rkl2_advance.argtypes = [c_void_p, c_void_p, c_double, POINTER(PbAdvanceOpts), POINTER(PbStats)]
     lib.be_pcg_advance.argtypes = [c_void_p, c_void_p, c_double, POINTER(PbAdvanceOpts), c_void_p, POINTER(PbStats)]
-    for name in ("parabolic_setup", "parabolic_destroy", "parabolic_state_size", "parabolic_dt_explicit",
+    lib.pb_profile_enable.argtypes = [c_void_p, c_int32]
+    lib.pb_profile_read.argtypes = [c_void_p, POINTER(PbKernelStat), c_int32, POINTER(c_int32)]
+    for name in ("pb_profile_enable", "pb_profile_read", "parabolic_setup", "parabolic_update", "parabolic_destroy", "parabolic_state_size", "parabolic_dt_explicit",
                  "parabolic_apply", "ptl_compute", "rkl2_advance", "be_pcg_advance"):
         getattr(lib, name).restype = c_int32
     _lib = lib
@@ -167,6 +175,20 @@ def parabolic_setup(r_face, t_face, n_phi: int, kind: str, fields: dict, precisi
     tf = (c_double * len(t_face))(*[float(x) for x in t_face])
     g = PbGrid(len(r_face) - 1, len(t_face) - 1, int(n_phi), ctypes.cast(rf, POINTER(c_double)),
                ctypes.cast(tf, POINTER(c_double)))
+    op, keep = _operator(kind, fields, C)
+    h = c_void_p()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib.parabolic_setup(byref(g), byref(op), PRECISIONS[precision], c_void_p(_stream_handle(st)), byref(h)))
+    n = c_int64()
+    e = c_int32()
+    _check(lib.parabolic_state_size(h, byref(n), byref(e)), h)
+    ctx = Context(h, kind, PRECISIONS[precision], st, n.value, e.value)
+    ctx.C = float(C)
+    return ctx
+
+
+def _operator(kind: str, fields: dict, C: float):
+    torch = _torch()
     op = PbOperator()
     keep = []
 
@@ -190,13 +212,13 @@ def parabolic_setup(r_face, t_face, n_phi: int, kind: str, fields: dict, precisi
             op.nu[a] = dptr(fields["nu"][a])
     else:
         raise ValueError(kind)
-    h = c_void_p()
-    st = stream if stream is not None else torch.cuda.current_stream()
-    _check(lib.parabolic_setup(byref(g), byref(op), PRECISIONS[precision], c_void_p(_stream_handle(st)), byref(h)))
-    n = c_int64()
-    e = c_int32()
-    _check(lib.parabolic_state_size(h, byref(n), byref(e)), h)
-    return Context(h, kind, PRECISIONS[precision], st, n.value, e.value)
+    return op, keep
+
+
+def parabolic_update(ctx: Context, fields: dict) -> None:
+    """Recomputes the frozen coefficients and dt_E in place from new operator fields."""
+    op, keep = _operator(ctx.kind, fields, getattr(ctx, "C", C_TC))
+    _check(load_library().parabolic_update(ctx.handle, byref(op)), ctx.handle)
 
 
 def parabolic_dt_explicit(ctx: Context) -> float:
@@ -304,5 +326,19 @@ def be_pcg_advance(ctx: Context, u, dt: float, use_ptl: bool = True, forced=None
     return d
 
 
-__all__ = ["parabolic_setup", "parabolic_dt_explicit", "parabolic_apply", "ptl_compute", "rkl2_advance",
+def pb_profile_enable(ctx: Context, on: bool = True) -> None:
+    """Resets the context's kernel counters; on=True also times every launch with CUDA events."""
+    _check(load_library().pb_profile_enable(ctx.handle, 1 if on else 0), ctx.handle)
+
+
+def pb_profile_read(ctx: Context) -> list:
+    """Per kernel class: name, launches, timed launches, total milliseconds, algorithmic bytes."""
+    buf = (PbKernelStat * 16)()
+    n = c_int32()
+    _check(load_library().pb_profile_read(ctx.handle, buf, 16, byref(n)), ctx.handle)
+    return [dict(name=buf[i].name.decode(), launches=buf[i].launches, timed_launches=buf[i].timed_launches,
+                 total_ms=buf[i].total_ms, bytes=buf[i].bytes) for i in range(n.value)]
+
+
+__all__ = ["pb_profile_enable", "pb_profile_read", "parabolic_setup", "parabolic_update", "parabolic_dt_explicit", "parabolic_apply", "ptl_compute", "rkl2_advance",
            "be_pcg_advance", "Context", "ParabolicError", "load_library", "EXPORTS"]

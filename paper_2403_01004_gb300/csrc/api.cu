@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 #include <limits>
 #include <new>
@@ -149,9 +150,14 @@ void build_grid(Ctx& c) {
 }
 
 void free_ctx(Ctx& c) {
+    cudaStreamSynchronize(c.stream);
+    c.prof.release();
     void* ptrs[] = {c.coef, c.coef_be, c.coef64, c.adiag, c.y0, c.buf[0], c.buf[1], c.buf[2], c.r, c.p[0],
                     c.p[1], c.q, c.dinv, c.partials, c.counter, c.d_ptl, c.d_pcg, c.d_scalar, c.d_flag, c.d_err};
     for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c.s64) cudaFree(c.s64);
+    for (double* p : c.geo)
         if (p) cudaFree(p);
     if (c.h_ptl) cudaFreeHost(c.h_ptl);
     if (c.h_pcg) cudaFreeHost(c.h_pcg);
@@ -173,6 +179,7 @@ void ensure_pcg_buffers(Ctx& c) {
 void sync(Ctx& c) {
     PB_CUDA_TRY(cudaMemcpyAsync(c.h_err, c.d_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     PB_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    c.prof.harvest();
     if (*c.h_err) {
         *c.h_err = 0;
         cudaMemsetAsync(c.d_err, 0, sizeof(int), c.stream);
@@ -234,6 +241,32 @@ void stats_cycle(pb_stats* st, double dt_c, int work, double dtp, long long k) {
         if (st->k_cycle) st->k_cycle[c] = k;
     }
     st->cycles = c + 1;
+}
+
+void check_operator(int kind, const pb_operator* op) {
+    if (!op) throw Error{PB_EINVAL, "null operator"};
+    if (op->kind != kind) throw Error{PB_EINVAL, "operator kind differs from the context's"};
+    if (kind == PB_TC_ANISO) {
+        if (!op->T0 || !op->n || !op->B[0] || !op->B[1] || !op->B[2]) throw Error{PB_EINVAL, "conduction needs T0, n, B"};
+        if (!(op->C > 0.0)) throw Error{PB_EINVAL, "C must be > 0"};
+    } else {
+        for (int a = 0; a < 3; ++a)
+            if (!op->rho[a] || !op->nu[a]) throw Error{PB_EINVAL, "viscosity needs rho[3], nu[3]"};
+    }
+}
+
+// (Re)computes the float64 records, diag(A) and dt_E, and stores them in the context precision.
+void update_coefficients(Ctx& c, const pb_operator& op) {
+    // set-up reads the float64 inputs and writes the float64 and stored records once
+    const double in_words = c.kind == PB_TC_ANISO ? 5.0 : 2.0;
+    {
+        KScope ks(c.prof, c.stream, K_SETUP, (double)c.n * (8.0 * in_words + 8.0 * 5 + 2.0 * 4 * (c.prec == PB_FP64 ? 8 : 4)));
+        if (c.kind == PB_TC_ANISO) setup_tc(c, op, c.coef64, &c.dt_e);
+        else setup_visc(c, op, c.coef64, &c.dt_e);
+        ops_of(c)->store_coefs(c, c.coef64, c.s64);
+    }
+    sync(c);
+    if (!(c.dt_e > 0.0) || std::isinf(c.dt_e)) throw Error{PB_ENONFINITE, "dt_E is not a positive finite number"};
 }
 
 // Runs the PTL pass on u (y0 = F(u) in c.y0) and returns the result (host).
@@ -306,15 +339,8 @@ int parabolic_setup(const pb_grid* g, const pb_operator* op, int32_t precision, 
             if (!(g->t_face[j + 1] > g->t_face[j])) throw Error{PB_EINVAL, "t_face must increase"};
         if ((long long)g->n_r * g->n_theta * g->n_phi > (1LL << 40)) throw Error{PB_EINVAL, "grid too large"};
         if (precision != PB_FP64 && precision != PB_FP32 && precision != PB_BF16_STORE) throw Error{PB_EINVAL, "bad precision"};
-        if (op->kind == PB_TC_ANISO) {
-            if (!op->T0 || !op->n || !op->B[0] || !op->B[1] || !op->B[2]) throw Error{PB_EINVAL, "conduction needs T0, n, B"};
-            if (!(op->C > 0.0)) throw Error{PB_EINVAL, "C must be > 0"};
-        } else if (op->kind == PB_VISC_ISO) {
-            for (int a = 0; a < 3; ++a)
-                if (!op->rho[a] || !op->nu[a]) throw Error{PB_EINVAL, "viscosity needs rho[3], nu[3]"};
-        } else {
-            throw Error{PB_EINVAL, "unknown operator kind"};
-        }
+        if (op->kind != PB_TC_ANISO && op->kind != PB_VISC_ISO) throw Error{PB_EINVAL, "unknown operator kind"};
+        check_operator(op->kind, op);
         int dev = 0;
         PB_CUDA_TRY(cudaGetDevice(&dev));
         pb_ctx* h = new pb_ctx();
@@ -354,25 +380,57 @@ int parabolic_setup(const pb_grid* g, const pb_operator* op, int32_t precision, 
             PB_CUDA_TRY(cudaMallocHost(&c.h_scalar, sizeof(double)));
             PB_CUDA_TRY(cudaMemsetAsync(c.counter, 0, sizeof(unsigned int), c.stream));
             PB_CUDA_TRY(cudaMemsetAsync(c.d_flag, 0, sizeof(int), c.stream));
-            // the float64 diag(A) goes through the PCG residual buffer's slot of y0 / buf space
-            double* adiag64 = static_cast<double*>(dmalloc((size_t)c.n * sizeof(double)));
-            try {
-                if (c.kind == PB_TC_ANISO) setup_tc(c, *g, *op, c.coef64, adiag64, &c.dt_e);
-                else setup_visc(c, *g, *op, c.coef64, adiag64, &c.dt_e);
-                ops_of(c)->store_coefs(c, c.coef64, adiag64);
-                sync(c);
-            } catch (...) {
-                cudaFree(adiag64);
-                throw;
-            }
-            cudaFree(adiag64);
-            if (!(c.dt_e > 0.0) || std::isinf(c.dt_e)) throw Error{PB_ENONFINITE, "dt_E is not a positive finite number"};
+            c.s64 = static_cast<double*>(dmalloc((size_t)c.n * sizeof(double)));
+            setup_geometry(c, *g);
+            update_coefficients(c, *op);
         } catch (...) {
             free_ctx(c);
             delete h;
             throw;
         }
         *out = h;
+    });
+}
+
+int parabolic_update(pb_ctx* h, const pb_operator* op) {
+    if (!h) return PB_EINVAL;
+    Ctx& c = h->c;
+    return guarded(&c, [&] {
+        check_operator(c.kind, op);
+        update_coefficients(c, *op);
+    });
+}
+
+int pb_profile_enable(pb_ctx* h, int32_t on) {
+    if (!h) return PB_EINVAL;
+    Ctx& c = h->c;
+    return guarded(&c, [&] {
+        sync(c);
+        c.prof.reset();
+        c.prof.on = on != 0;
+    });
+}
+
+int pb_profile_read(pb_ctx* h, pb_kernel_stat* out, int32_t cap, int32_t* count) {
+    if (!h) return PB_EINVAL;
+    Ctx& c = h->c;
+    return guarded(&c, [&] {
+        sync(c);
+        int n = 0;
+        for (int k = 0; k < K_NCLASS; ++k) {
+            if (c.prof.launches[k] == 0) continue;
+            if (out && n < cap) {
+                pb_kernel_stat& s = out[n];
+                std::memset(&s, 0, sizeof(s));
+                std::snprintf(s.name, sizeof(s.name), "%s.%s", c.kind == PB_TC_ANISO ? "tc" : "visc", kclass_name(k));
+                s.launches = c.prof.launches[k];
+                s.timed_launches = c.prof.timed[k];
+                s.total_ms = c.prof.ms[k];
+                s.bytes = c.prof.bytes[k];
+            }
+            ++n;
+        }
+        if (count) *count = n;
     });
 }
 
@@ -460,14 +518,17 @@ int rkl2_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, pb_
                 }
             }
             make_sts(o.scheme, dt_c / c.dt_e, co);
-            // stage loop in increment form d_k = u_k - u_0 (see EpiStage): d_1 = mut_1 dt y0 in
-            // buf[0]; buffers rotate over buf[0..2]; the last stage writes u_0 + d_s into u
+            // stage loop in increment form d_k = u_k - u_0 (see EpiStage): y0 = F(u0) (from the
+            // PTL pass, or computed here), stages 1 and 2 fused (d1 = mut_1 dt y0 in buf[0]),
+            // d_k in buf[(k-1) % 3], and the last stage writes u_0 + d_s into u
             const double a1 = co.mut[1] * dt_c;
-            if (y0_done) ops->stage1(c, c.y0, c.buf[0], a1);
-            else ops->y0_pass(c, u, c.y0, false, c.buf[0], a1);
-            for (int k = 2; k <= co.s; ++k) {
+            if (!y0_done) ops->apply(c, u, c.y0);
+            const StageCoef k2{co.mu[2], co.nu[2], co.mut[2] * dt_c, (co.mut[2] + co.gt[2]) * dt_c};
+            if (co.s == 2) ops->stage2(c, c.y0, nullptr, u, u, a1, k2);
+            else ops->stage2(c, c.y0, c.buf[0], nullptr, c.buf[1], a1, k2);
+            for (int k = 3; k <= co.s; ++k) {
                 const void* dkm1 = c.buf[(k - 2) % 3];
-                const void* dkm2 = k == 2 ? nullptr : c.buf[(k - 3) % 3];
+                const void* dkm2 = c.buf[(k - 3) % 3];
                 const bool last = k == co.s;
                 void* out = last ? u : c.buf[(k - 1) % 3];
                 ops->stage(c, dkm1, dkm2, last ? u : nullptr, c.y0, out,

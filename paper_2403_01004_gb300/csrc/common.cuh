@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/parabolic.h"
+#include "prof.h"
 
 namespace pb {
 
@@ -122,6 +123,10 @@ struct Ctx {
     PtlResult* h_ptl = nullptr;
     PcgScalars* h_pcg = nullptr;
     double* h_scalar = nullptr;
+    // persistent set-up workspace (coefficient updates allocate nothing)
+    double* s64 = nullptr;         // float64 scratch [n]: kappa, then diag(A)
+    double* geo[16] = {};          // device copies of the face / point coordinate arrays
+    Prof prof;
     std::string err;
     int sm_count = 0;
 };

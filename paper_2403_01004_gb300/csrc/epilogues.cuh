@@ -55,11 +55,11 @@ struct EpiF {
     A a;
     ArgMax* part;
     int* nonfinite;
-    double bv;
-    long long bi;
+    A bv;            // running max |F| of this thread, compared in the arithmetic precision (the
+    long long bi;    // stored F converts exactly, so the decision equals a float64 comparison)
     int bad;
     static constexpr int NC = 0;     // point operands delivered by the TMA kernel
-    __device__ void init() { bv = -1.0; bi = LLONG_MAX; bad = 0; }
+    __device__ void init() { bv = A(-1); bi = LLONG_MAX; bad = 0; }
     __device__ bool skip() const { return false; }
     __device__ Pre prefetch(long long) const { return {}; }
     __device__ void apply_c(long long idx, A Au, A w, A center, A, A, A) { apply(idx, Au, w, center, Pre{}); }
@@ -69,16 +69,18 @@ struct EpiF {
         F[idx] = fs;
         if (U1) u1[idx] = cvt<S>(a * f);
         if (ARGMAX) {
-            const double v = fabs((double)cvt<A>(fs));
-            if (!(v <= 1.79769313486231570e308)) bad = 1;
-            else argmax_merge(bv, bi, v, idx);
+            const A v = fabs(cvt<A>(fs));
+            if (!isfinite(v)) bad = 1;
+            else if (v > bv) { bv = v; bi = idx; }   // a thread visits its indices in rising order
         }
     }
     __device__ void finish() {
         if (!ARGMAX) return;
         if (bad) atomicOr(nonfinite, 1);
-        block_argmax(bv, bi);
-        if (threadIdx.x == 0 && threadIdx.y == 0) part[blockIdx.x] = ArgMax{bv, bi};
+        double v = (double)bv;
+        long long i = bi;
+        block_argmax(v, i);
+        if (threadIdx.x == 0 && threadIdx.y == 0) part[blockIdx.x] = ArgMax{v, i};
     }
 };
 
@@ -113,6 +115,37 @@ struct EpiStage {
     __device__ void apply(long long idx, A Au, A w, A dkm1, const Pre& p) {
         const A d = mu * dkm1 + nu * p.dkm2 + mdt * (w * Au) + ydt * p.y0;
         out[idx] = cvt<S>(LAST ? p.u0 + d : d);
+    }
+    __device__ void finish() {}
+};
+
+// STS stage 2 fused with stage 1.  The march runs on y0 itself: with d1 = a y0 and the linear
+// operator, F(d1) = a F(y0), so
+//   d2 = mu_2 d1 + mut_2 dt F(d1) + (mut_2 + gt_2) dt y0 = (mu_2 a + ydt) y0 + (mdt a) F(y0),
+// and d1 is written (for stage 3) only when s > 2; when s = 2 this is the last stage and
+// u0 + d2 is written over u0.
+template <class P, bool LAST>
+struct EpiStage2 {
+    using A = typename P::A;
+    using S = typename P::S;
+    struct Pre { A u0; };
+    const S* u0;
+    S* d1;
+    S* out;
+    A a, cy, cf;       // a = mut_1 dt, cy = mu_2 a + ydt, cf = mdt a
+    static constexpr int NC = LAST ? 1 : 0;
+    __device__ void init() {}
+    __device__ bool skip() const { return false; }
+    __device__ Pre prefetch(long long idx) const { return Pre{LAST ? cvt<A>(u0[idx]) : A(0)}; }
+    __device__ void apply_c(long long idx, A Au, A w, A y, A c0, A, A) { apply(idx, Au, w, y, Pre{c0}); }
+    __device__ void apply(long long idx, A Au, A w, A y, const Pre& p) {
+        const A d2 = cy * y + cf * (w * Au);
+        if (LAST) {
+            out[idx] = cvt<S>(p.u0 + d2);
+        } else {
+            d1[idx] = cvt<S>(a * y);
+            out[idx] = cvt<S>(d2);
+        }
     }
     __device__ void finish() {}
 };

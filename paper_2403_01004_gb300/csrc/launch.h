@@ -20,6 +20,10 @@ public:
     virtual void ptl_finalize(Ctx& c, const void* u, const void* F) = 0;
     // d1 = a y0
     virtual void stage1(Ctx& c, const void* y0, void* d1, double a) = 0;
+    // stages 1 and 2 fused (EpiStage2): from y0, writes d1 (when u0 == nullptr) and d2 into out,
+    // or u0 + d2 into out when u0 != nullptr (s = 2)
+    virtual void stage2(Ctx& c, const void* y0, void* d1, const void* u0, void* out, double a1,
+                        const StageCoef& k) = 0;
     // one STS stage k >= 2 on increments; dkm2 == nullptr means d_{k-2} = 0 (k = 2); u0 !=
     // nullptr marks the last stage, which writes u0 + d_s into out
     virtual void stage(Ctx& c, const void* dkm1, const void* dkm2, const void* u0, const void* y0,
@@ -36,11 +40,10 @@ Ops* ops_f64();
 Ops* ops_f32();
 Ops* ops_b16();
 
-// set-up kernels (float64), see setup.cu
-void setup_tc(Ctx& c, const pb_grid& g, const pb_operator& op, Coef4<double>* rec, double* adiag,
-              double* dt_e);
-void setup_visc(Ctx& c, const pb_grid& g, const pb_operator& op, Coef4<double>* rec, double* adiag,
-                double* dt_e);
+// set-up kernels (float64), see setup.cu.  setup_tc / setup_visc leave diag(A) in c.s64.
+void setup_geometry(Ctx& c, const pb_grid& g);
+void setup_tc(Ctx& c, const pb_operator& op, Coef4<double>* rec, double* dt_e);
+void setup_visc(Ctx& c, const pb_operator& op, Coef4<double>* rec, double* dt_e);
 
 int reduce_blocks(const Ctx& c);   // grid size of the element-wise reduction kernels
 

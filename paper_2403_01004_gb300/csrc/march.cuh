@@ -181,16 +181,17 @@ tc_march(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld_in,
 }
 
 // ---------------------------------------------------------------------------------------------
-// Viscosity march kernel (all three components in one launch).
+// Viscosity march kernel (all three components in one launch).  The 7-point stencil reuses
+// little in a tile, so there is no shared-memory staging and no barrier: each thread walks its
+// (r, theta) column along phi keeping planes k-1, k, k+1 of its own point in registers, reads
+// the four in-plane neighbours (other threads' points, served by L1 / L2) and prefetches the
+// next plane's operands one iteration ahead.
 // ---------------------------------------------------------------------------------------------
 template <class P, class Load, class Epi>
 __global__ void __launch_bounds__(NTHREADS)
 visc_march(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld_in, Epi ep_in) {
     using A = typename P::A;
     using C = typename P::C;
-    __shared__ A us[TY + 2][TX + 2];
-    __shared__ A crs[TY][TX + 1];
-    __shared__ A cts[TY + 1][TX];
 
     Epi ep = ep_in;
     ep.init();
@@ -202,71 +203,56 @@ visc_march(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld_i
     const CompGrid& cg = g.c[t.comp];
     const int nr = cg.nr, nt = cg.nt, np = cg.np;
     const long long plane = (long long)nr * nt;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i = t.i0 + tx, j = t.j0 + ty;
+    const int i = t.i0 + threadIdx.x, j = t.j0 + threadIdx.y;
     const bool own = (i < nr) && (j < nt);
-
-    auto gidx = [&](int gi, int gj, int kk) -> long long {
-        return cg.offset + (long long)wrap_phi(kk, np) * plane + (long long)gj * nr + gi;
-    };
-    auto fetch = [&](int gi, int gj, int kk) -> A {
-        if (gi < 0 || gi >= nr || gj < 0 || gj >= nt) return A(0);
-        return ld(gidx(gi, gj, kk));
-    };
-    auto fetch_coef = [&](int gi, int gj, int kk) -> Coef4<A> {
-        if (gi < 0 || gi >= nr || gj < 0 || gj >= nt) return Coef4<A>{A(0), A(0), A(0), A(0)};
-        return load_coef<A, C>(coef + gidx(gi, gj, kk));
-    };
-
-    // registers: u of this point at planes k-1, k, k+1; its -phi face coefficient; and a
-    // one-plane prefetch of everything plane k+1 needs
-    A ukm = fetch(i, j, t.k0 - 1);
-    A uk = fetch(i, j, t.k0);
-    A ukp = fetch(i, j, t.k0 + 1);
-    A cpm = fetch_coef(i, j, t.k0 - 1).c;
-    Coef4<A> nc = fetch_coef(i, j, t.k0);
-    A n_ul = tx == 0 ? fetch(i - 1, j, t.k0) : A(0);
-    A n_ur = tx == TX - 1 ? fetch(i + 1, j, t.k0) : A(0);
-    A n_ub = ty == 0 ? fetch(i, j - 1, t.k0) : A(0);
-    A n_ut = ty == TY - 1 ? fetch(i, j + 1, t.k0) : A(0);
-    A n_crl = tx == 0 ? fetch_coef(i - 1, j, t.k0).a : A(0);
-    A n_ctb = ty == 0 ? fetch_coef(i, j - 1, t.k0).b : A(0);
-    typename Epi::Pre npre{};
-    if (own) npre = ep.prefetch(gidx(i, j, t.k0));
-
-    for (int k = t.k0; k < t.k1; ++k) {
-        const long long idx = gidx(i, j, k);
-        const Coef4<A> c = nc;
-        const typename Epi::Pre pre = npre;
-        us[ty + 1][tx + 1] = uk;
-        crs[ty][tx + 1] = c.a;
-        cts[ty + 1][tx] = c.b;
-        if (tx == 0) { us[ty + 1][0] = n_ul; crs[ty][0] = n_crl; }
-        if (tx == TX - 1) us[ty + 1][TX + 1] = n_ur;
-        if (ty == 0) { us[0][tx + 1] = n_ub; cts[0][tx] = n_ctb; }
-        if (ty == TY - 1) us[TY + 1][tx + 1] = n_ut;
-        A ukpp = A(0);
-        if (k + 1 < t.k1) {
-            ukpp = fetch(i, j, k + 2);
-            nc = fetch_coef(i, j, k + 1);
-            if (tx == 0) { n_ul = fetch(i - 1, j, k + 1); n_crl = fetch_coef(i - 1, j, k + 1).a; }
-            if (tx == TX - 1) n_ur = fetch(i + 1, j, k + 1);
-            if (ty == 0) { n_ub = fetch(i, j - 1, k + 1); n_ctb = fetch_coef(i, j - 1, k + 1).b; }
-            if (ty == TY - 1) n_ut = fetch(i, j + 1, k + 1);
-            if (own) npre = ep.prefetch(gidx(i, j, k + 1));
+    if (own) {
+        const bool rm = i > 0, rp = i < nr - 1, tm = j > 0, tp = j < nt - 1;
+        const long long col = cg.offset + (long long)j * nr + i;
+        auto at = [&](int kk) -> long long {
+            kk = kk < 0 ? kk + np : (kk >= np ? kk - np : kk);
+            return col + (long long)kk * plane;
+        };
+        // in-plane operands of one phi plane (the point's own value travels separately)
+        struct Plane { A urm, urp, utm, utp, crm, ctm; Coef4<A> c; };
+        auto fetch = [&](long long idx) -> Plane {
+            Plane q;
+            q.urm = rm ? ld(idx - 1) : A(0);
+            q.urp = rp ? ld(idx + 1) : A(0);
+            q.utm = tm ? ld(idx - nr) : A(0);
+            q.utp = tp ? ld(idx + nr) : A(0);
+            q.c = load_coef<A, C>(coef + idx);
+            q.crm = rm ? (A)__ldg(&coef[idx - 1].a) : A(0);
+            q.ctm = tm ? (A)__ldg(&coef[idx - nr].b) : A(0);
+            return q;
+        };
+        A ukm = ld(at(t.k0 - 1));
+        A cpm = (A)__ldg(&coef[at(t.k0 - 1)].c);
+        long long idx = at(t.k0);
+        A uk = ld(idx);
+        Plane cur = fetch(idx);
+        A ukp = ld(at(t.k0 + 1));
+        typename Epi::Pre pre = ep.prefetch(idx);
+        for (int k = t.k0; k < t.k1; ++k) {
+            Plane nxt{};
+            A ukpp = A(0);
+            typename Epi::Pre npre{};
+            const long long idn = at(k + 1);
+            if (k + 1 < t.k1) {
+                nxt = fetch(idn);
+                ukpp = ld(at(k + 2));
+                npre = ep.prefetch(idn);
+            }
+            const A Au = cur.c.a * (cur.urp - uk) + cur.crm * (cur.urm - uk) + cur.c.b * (cur.utp - uk)
+                       + cur.ctm * (cur.utm - uk) + cur.c.c * (ukp - uk) + cpm * (ukm - uk);
+            ep.apply(idx, Au, cur.c.w, uk, pre);
+            ukm = uk;
+            uk = ukp;
+            ukp = ukpp;
+            cpm = cur.c.c;
+            cur = nxt;
+            pre = npre;
+            idx = idn;
         }
-        __syncthreads();
-        if (own) {
-            const A Au = crs[ty][tx + 1] * (us[ty + 1][tx + 2] - uk) + crs[ty][tx] * (us[ty + 1][tx] - uk)
-                       + cts[ty + 1][tx] * (us[ty + 2][tx + 1] - uk) + cts[ty][tx] * (us[ty][tx + 1] - uk)
-                       + c.c * (ukp - uk) + cpm * (ukm - uk);
-            ep.apply(idx, Au, c.w, uk, pre);
-        }
-        __syncthreads();
-        ukm = uk;
-        uk = ukp;
-        ukp = ukpp;
-        cpm = c.c;
     }
     ep.finish();
 }

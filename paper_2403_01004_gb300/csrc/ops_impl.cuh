@@ -55,7 +55,12 @@ class OpsImpl : public Ops {
 public:
     bool supports_pcg() const override { return P::id != PB_BF16_STORE; }
 
+    static double nb(const Ctx& c, double s_words, double c_words) {
+        return (double)c.n * (s_words * sizeof(S) + c_words * sizeof(C));
+    }
+
     void apply(Ctx& c, const void* u, void* F) override {
+        KScope ks(c.prof, c.stream, K_APPLY, nb(c, 2, 4));
         EpiF<P, false, false> ep{static_cast<S*>(F), nullptr, A(0), nullptr, nullptr};
         march_state(c, u, nullptr, ep);
     }
@@ -64,6 +69,7 @@ public:
         ArgMax* part = static_cast<ArgMax*>(c.partials);
         if (argmax) {
             PB_CUDA_TRY(cudaMemsetAsync(c.d_flag, 0, sizeof(int), c.stream));
+            KScope ks(c.prof, c.stream, K_PTL_PASS, nb(c, u1 ? 3 : 2, 4));
             if (u1) {
                 EpiF<P, true, true> ep{static_cast<S*>(y0), static_cast<S*>(u1), (A)a, part, c.d_flag};
                 march_state(c, u, nullptr, ep);
@@ -72,6 +78,7 @@ public:
                 march_state(c, u, nullptr, ep);
             }
         } else if (u1) {
+            KScope ks(c.prof, c.stream, K_Y0_D1, nb(c, 3, 4));
             EpiF<P, false, true> ep{static_cast<S*>(y0), static_cast<S*>(u1), (A)a, nullptr, nullptr};
             march_state(c, u, nullptr, ep);
         } else {
@@ -80,6 +87,7 @@ public:
     }
 
     void ptl_finalize(Ctx& c, const void* u, const void* F) override {
+        KScope ks(c.prof, c.stream, K_PTL_FINAL, (double)c.grid.nblocks * sizeof(ArgMax));
         ptl_finalize_kernel<P><<<1, 256, 0, c.stream>>>(c.grid, static_cast<const S*>(u), static_cast<const S*>(F),
                                                         static_cast<const ArgMax*>(c.partials), c.grid.nblocks,
                                                         c.d_ptl, c.d_flag);
@@ -88,8 +96,23 @@ public:
 
     void stage1(Ctx& c, const void* y0, void* d1, double a) override {
         const int blocks = reduce_blocks(c);
+        KScope ks(c.prof, c.stream, K_STAGE1, nb(c, 2, 0));
         stage1_kernel<P><<<blocks, 256, 0, c.stream>>>(c.n, static_cast<const S*>(y0), static_cast<S*>(d1), (A)a);
         PB_CUDA_TRY(cudaGetLastError());
+    }
+
+    template <bool LAST>
+    void stage2_t(Ctx& c, const void* y0, void* d1, const void* u0, void* out, double a1, const StageCoef& k) {
+        KScope ks(c.prof, c.stream, K_STAGE, nb(c, 3, 4));
+        EpiStage2<P, LAST> ep{static_cast<const S*>(u0), static_cast<S*>(d1), static_cast<S*>(out), (A)a1,
+                              (A)(k.mu * a1 + k.ydt), (A)(k.mdt * a1)};
+        const void* cen[1] = {u0};
+        march_state(c, y0, cen, ep);
+    }
+
+    void stage2(Ctx& c, const void* y0, void* d1, const void* u0, void* out, double a1, const StageCoef& k) override {
+        if (u0) stage2_t<true>(c, y0, d1, u0, out, a1, k);
+        else stage2_t<false>(c, y0, d1, u0, out, a1, k);
     }
 
     template <bool KM2, bool LAST>
@@ -97,6 +120,7 @@ public:
                  const StageCoef& k) {
         EpiStage<P, KM2, LAST> ep{static_cast<const S*>(dkm2), static_cast<const S*>(y0), static_cast<const S*>(u0),
                                   static_cast<S*>(out), (A)k.mu, (A)k.nu, (A)k.mdt, (A)k.ydt};
+        KScope ks(c.prof, c.stream, K_STAGE, nb(c, 3 + (KM2 ? 1 : 0) + (LAST ? 1 : 0), 4));
         const void* cen[3];
         int n = 0;
         cen[n++] = y0;
@@ -117,6 +141,7 @@ public:
     }
 
     void pcg_init(Ctx& c, const void* x, const void* un, double dt) override {
+        KScope ks(c.prof, c.stream, K_PCG_INIT, nb(c, 4, 5));
         EpiPcgInit<P> ep{static_cast<const S*>(un), static_cast<S*>(c.r), static_cast<S*>(c.dinv),
                          static_cast<const C*>(c.adiag), c.d_pcg, static_cast<double*>(c.partials),
                          c.counter, c.grid.nblocks, (A)dt};
@@ -129,8 +154,12 @@ public:
         LoadPcgP<P> ld{static_cast<const S*>(c.r), static_cast<const S*>(c.dinv), pold, c.d_pcg, A(0), 0};
         EpiPcgSpmv<P> ep{pnew, static_cast<S*>(c.q), c.d_pcg, static_cast<double*>(c.partials), c.counter,
                          c.grid.nblocks, (A)dt};
-        march(c, c.coef_be, ld, ep);
+        {
+            KScope ks(c.prof, c.stream, K_PCG_SPMV, nb(c, 5, 4));
+            march(c, c.coef_be, ld, ep);
+        }
         const int blocks = reduce_blocks(c);
+        KScope ks(c.prof, c.stream, K_PCG_UPDATE, nb(c, 7, 0));
         pcg_update_kernel<P><<<blocks, 256, 0, c.stream>>>(c.n, static_cast<S*>(x), static_cast<S*>(c.r), pnew,
                                                            static_cast<const S*>(c.q), static_cast<const S*>(c.dinv),
                                                            c.d_pcg, static_cast<double*>(c.partials), c.counter);

@@ -226,51 +226,58 @@ int setup_blocks(const Ctx& c, long long n) {
 
 int reduce_blocks(const Ctx& c) { return setup_blocks(c, c.n); }
 
-void setup_tc(Ctx& c, const pb_grid& g, const pb_operator& op, Coef4<double>* rec, double* adiag, double* dt_e) {
-    const long long n = c.n;
-    std::vector<double> rf(g.r_face, g.r_face + g.n_r + 1), tf(g.t_face, g.t_face + g.n_theta + 1);
-    double* drf = dev_copy(rf, c.stream);
-    double* dtf = dev_copy(tf, c.stream);
-    double* kap = nullptr;
-    PB_CUDA_TRY(cudaMalloc(&kap, n * sizeof(double)));
-    const int blocks = setup_blocks(c, n);
-    kappa_kernel<<<blocks, 256, 0, c.stream>>>(n, op.T0, kap);
-    TCArgs a{g.n_r, g.n_theta, g.n_phi, 2.0 * M_PI / g.n_phi, op.C, drf, dtf, kap, op.n, op.B[0], op.B[1], op.B[2], rec};
-    tc_coef_kernel<<<blocks, 256, 0, c.stream>>>(a);
-    double* part = static_cast<double*>(c.partials);
-    tc_rows_kernel<<<blocks, 256, 0, c.stream>>>(g.n_r, g.n_theta, g.n_phi, rec, adiag, part);
-    max_finalize_kernel<<<1, 256, 0, c.stream>>>(part, blocks, c.d_scalar);
-    PB_CUDA_TRY(cudaGetLastError());
-    PB_CUDA_TRY(cudaMemcpyAsync(c.h_scalar, c.d_scalar, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-    PB_CUDA_TRY(cudaStreamSynchronize(c.stream));
-    *dt_e = *c.h_scalar;
-    cudaFree(kap);
-    cudaFree(drf);
-    cudaFree(dtf);
-}
-
-void setup_visc(Ctx& c, const pb_grid& g, const pb_operator& op, Coef4<double>* rec, double* adiag, double* dt_e) {
+// Copies the face arrays (conduction) or the per-component point / bound arrays (viscosity) to
+// the device once per context.
+void setup_geometry(Ctx& c, const pb_grid& g) {
     const int nr = g.n_r, nt = g.n_theta;
     std::vector<double> rf(g.r_face, g.r_face + nr + 1), tf(g.t_face, g.t_face + nt + 1);
+    if (c.kind == PB_TC_ANISO) {
+        c.geo[0] = dev_copy(rf, c.stream);
+        c.geo[1] = dev_copy(tf, c.stream);
+        return;
+    }
     std::vector<double> rc(nr), tc(nt);
     for (int i = 0; i < nr; ++i) rc[i] = 0.5 * (rf[i] + rf[i + 1]);
     for (int j = 0; j < nt; ++j) tc[j] = 0.5 * (tf[j] + tf[j + 1]);
-    std::vector<double*> owned;
-    double* part = static_cast<double*>(c.partials);
-    int total_blocks = 0;
     for (int comp = 0; comp < 3; ++comp) {
-        const CompGrid& cg = c.grid.c[comp];
         std::vector<double> pr, er, pt, et;
         if (comp == 0) { pr.assign(rf.begin() + 1, rf.begin() + nr); er = rc; }
         else { pr = rc; er = rf; }
         if (comp == 1) { pt.assign(tf.begin() + 1, tf.begin() + nt); et = tc; }
         else { pt = tc; et = tf; }
-        double* dpr = dev_copy(pr, c.stream); double* der = dev_copy(er, c.stream);
-        double* dpt = dev_copy(pt, c.stream); double* det = dev_copy(et, c.stream);
-        owned.insert(owned.end(), {dpr, der, dpt, det});
+        c.geo[4 * comp + 0] = dev_copy(pr, c.stream);
+        c.geo[4 * comp + 1] = dev_copy(er, c.stream);
+        c.geo[4 * comp + 2] = dev_copy(pt, c.stream);
+        c.geo[4 * comp + 3] = dev_copy(et, c.stream);
+    }
+}
+
+void setup_tc(Ctx& c, const pb_operator& op, Coef4<double>* rec, double* dt_e) {
+    const long long n = c.n;
+    double* kap = c.s64;
+    const int blocks = setup_blocks(c, n);
+    kappa_kernel<<<blocks, 256, 0, c.stream>>>(n, op.T0, kap);
+    TCArgs a{c.nr, c.nt, c.np, 2.0 * M_PI / c.np, op.C, c.geo[0], c.geo[1], kap, op.n, op.B[0], op.B[1], op.B[2], rec};
+    tc_coef_kernel<<<blocks, 256, 0, c.stream>>>(a);
+    double* part = static_cast<double*>(c.partials);
+    double* adiag = c.s64;   // kappa is no longer needed
+    tc_rows_kernel<<<blocks, 256, 0, c.stream>>>(c.nr, c.nt, c.np, rec, adiag, part);
+    max_finalize_kernel<<<1, 256, 0, c.stream>>>(part, blocks, c.d_scalar);
+    PB_CUDA_TRY(cudaGetLastError());
+    PB_CUDA_TRY(cudaMemcpyAsync(c.h_scalar, c.d_scalar, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    PB_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    *dt_e = *c.h_scalar;
+}
+
+void setup_visc(Ctx& c, const pb_operator& op, Coef4<double>* rec, double* dt_e) {
+    double* part = static_cast<double*>(c.partials);
+    double* adiag = c.s64;
+    int total_blocks = 0;
+    for (int comp = 0; comp < 3; ++comp) {
+        const CompGrid& cg = c.grid.c[comp];
         const long long n = (long long)cg.nr * cg.nt * cg.np;
-        ViscArgs a{cg.nr, cg.nt, cg.np, 2.0 * M_PI / g.n_phi, dpr, der, dpt, det, op.rho[comp], op.nu[comp],
-                   rec + cg.offset};
+        ViscArgs a{cg.nr, cg.nt, cg.np, 2.0 * M_PI / c.np, c.geo[4 * comp], c.geo[4 * comp + 1], c.geo[4 * comp + 2],
+                   c.geo[4 * comp + 3], op.rho[comp], op.nu[comp], rec + cg.offset};
         const int blocks = setup_blocks(c, n);
         visc_coef_kernel<<<blocks, 256, 0, c.stream>>>(a);
         visc_rows_kernel<<<blocks, 256, 0, c.stream>>>(cg.nr, cg.nt, cg.np, rec + cg.offset, adiag + cg.offset,
@@ -282,7 +289,6 @@ void setup_visc(Ctx& c, const pb_grid& g, const pb_operator& op, Coef4<double>* 
     PB_CUDA_TRY(cudaMemcpyAsync(c.h_scalar, c.d_scalar, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     PB_CUDA_TRY(cudaStreamSynchronize(c.stream));
     *dt_e = *c.h_scalar;
-    for (double* p : owned) cudaFree(p);
 }
 
 }  // namespace pb
