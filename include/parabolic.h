@@ -196,6 +196,33 @@ PB_API int pb_profile_enable(pb_ctx* ctx, int32_t on);
 /* Writes up to cap records (classes with at least one launch) and their number to *count. */
 PB_API int pb_profile_read(pb_ctx* ctx, pb_kernel_stat* out, int32_t cap, int32_t* count);
 
+/* ---- PTL without allocation ---------------------------------------------------------------- */
+/* PTL of a state (the same result as ptl_compute) for callers that cannot allocate device
+ * memory: a host code that hands the solver a fixed, pre-sized device arena for a whole run, or
+ * one that cannot afford the device-wide synchronisation and failure modes of cudaMalloc /
+ * cudaFree inside its time-step loop.  It needs no context and allocates nothing (no cudaMalloc,
+ * no cudaFree, no allocating library call): the caller passes
+ *   records  the operator's packed per-point records, n Coef4 entries in the layout the library
+ *            uses (conduction: {ahat_r, ahat_t, ahat_p} of corner [i,j,k] and the cell weight w;
+ *            viscosity: {c_r, c_t, c_p} of the +1 faces and w), float64 for PB_FP64, float32 for
+ *            PB_FP32 and PB_BF16_STORE;
+ *   u        the state (n elements of the precision's storage type), read only;
+ *   F        output, n elements: F = L u;
+ * and receives dt_ptl, k_index and fmax on the host (any may be NULL).  n is n_r*n_theta*n_phi
+ * for conduction and the three-component total for viscosity.  The paper has no counterpart:
+ * this is a deployment variant of the PTL pass.
+ * Its only scratch (per-block partials, a flag, the result) is one file-scope device array of
+ * 1 MiB that every GPU loading the library holds until exit; grids needing more than 65,520
+ * partial records (more than that many 32 x 8 (r, theta) tiles) are rejected with PB_EINVAL.
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress); make
+ * it before any stream capture.  Every call shares the array, so calls whose work overlaps on
+ * the GPU (other streams, other host threads) race; serialise them.  Work runs on `stream`
+ * (cudaStream_t, NULL = legacy default) and the call returns after it completes.
+ * Returns PB_OK, PB_EINVAL, PB_ENONFINITE (non-finite F) or PB_ECUDA. */
+PB_API int pb_ptl_noalloc(int32_t kind, int32_t n_r, int32_t n_theta, int32_t n_phi,
+                          int32_t precision, const void* records, const void* u, void* F,
+                          double* dt_ptl, int64_t* k_index, double* fmax, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,8 @@ C_TC = (5.0 / 3.0 - 1.0) / 2.0
 # C function names exported by the library (kept in step with include/parabolic.h)
 EXPORTS = ("pb_advance_opts_init", "pb_status_string", "pb_last_error", "parabolic_setup",
            "parabolic_update", "parabolic_destroy", "parabolic_state_size", "parabolic_dt_explicit", "parabolic_apply",
-           "ptl_compute", "rkl2_advance", "be_pcg_advance", "pb_profile_enable", "pb_profile_read")
+           "ptl_compute", "rkl2_advance", "be_pcg_advance", "pb_profile_enable", "pb_profile_read",
+           "pb_ptl_noalloc")
 
 
 class PbGrid(ctypes.Structure):
@@ -94,6 +95,9 @@ def load_library(path: str = LIB_PATH):
     lib.ptl_compute.argtypes = [c_void_p, c_void_p, POINTER(c_double), POINTER(c_int64), POINTER(c_double)]
     lib.rkl2_advance.argtypes = [c_void_p, c_void_p, c_double, POINTER(PbAdvanceOpts), POINTER(PbStats)]
     lib.be_pcg_advance.argtypes = [c_void_p, c_void_p, c_double, POINTER(PbAdvanceOpts), c_void_p, POINTER(PbStats)]
+    lib.pb_ptl_noalloc.argtypes = [c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
+                                   POINTER(c_double), POINTER(c_int64), POINTER(c_double), c_void_p]
+    lib.pb_ptl_noalloc.restype = c_int32
     lib.pb_profile_enable.argtypes = [c_void_p, c_int32]
     lib.pb_profile_read.argtypes = [c_void_p, POINTER(PbKernelStat), c_int32, POINTER(c_int32)]
     for name in ("pb_profile_enable", "pb_profile_read", "parabolic_setup", "parabolic_update", "parabolic_destroy", "parabolic_state_size", "parabolic_dt_explicit",
