@@ -54,6 +54,7 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-pcg", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-launch sub-benchmark")
     return ap.parse_args()
 
 
@@ -273,6 +274,8 @@ def run_ours(args):
     extra = {}
     if not args.no_pcg:
         extra["pcg"] = pcg_probe(pb, torch, ctx_tc, d_tc, d_u0, u, wl)
+    if not args.no_batch:
+        extra["batched"] = batched_probe(pb, torch)
     if not args.no_fp64 and args.precision != "fp64":
         extra["fp64_plain"] = fp64_probe(pb, torch, g, d_tc, d_vi, d_u0, d_v0, wl, args, value)
     cpu = None
@@ -347,6 +350,55 @@ def pcg_probe(pb, torch, ctx_tc, d_tc, d_u0, u, wl):
     ms = e0.elapsed_time(e1)
     return {"what": "BE + point-Jacobi PCG, conduction, dt = 1e3 dt_E, 50 iterations (fixed)",
             "ms_per_iteration": ms / iters, "point_iterations_per_s": ctx_tc.n * iters / (ms / 1e3)}
+
+
+def batched_probe(pb, torch, reps=3):
+    """The batched workload: 64 conduction problems (n_r, n_theta in {16..128}, n_phi in
+    {n_theta, 2 n_theta}, dt/dt_E log-uniform in [10, 1e4], tilted dipoles), float32, advanced by
+    one autotuned persistent graph launch, against the same problems advanced one by one."""
+    import synth
+    from synth import device
+    probs = synth.batched_problems()
+    ctxs, u0s, dts = [], [], []
+    for pr in probs:
+        g = synth.make_grid(pr["n_r"], pr["n_t"], pr["n_p"], pr["q"])
+        inp = synth.tc_inputs(g, pr["seed"], m=pr["m"])
+        ctx = pb.parabolic_setup(g.r_face, g.t_face, g.n_phi, "tc", device.tc_fields(inp), "fp32")
+        ctxs.append(ctx)
+        u0s.append(torch.from_numpy(inp.T.reshape(-1)).to("cuda", torch.float32))
+        dts.append(pr["ratio"] * pb.parabolic_dt_explicit(ctx))
+    us = [u.clone() for u in u0s]
+    batch = pb.pb_batch_create(ctxs)
+    tune, tune_ms = pb.pb_autotune(batch, us, dts)
+    st = pb.pb_batch_rkl2_advance(batch, us, dts)
+    units = sum(c.n * x["total_stages"] for c, x in zip(ctxs, st))
+
+    def timed(fn):
+        best = 1e30
+        for _ in range(reps):
+            for u, u0 in zip(us, u0s):
+                u.copy_(u0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    ms_b = timed(lambda: pb.pb_batch_rkl2_advance(batch, us, dts))
+    ms_s = timed(lambda: [pb.rkl2_advance(c, u, dt, use_ptl=False) for c, u, dt in zip(ctxs, us, dts)])
+    stages = [x["total_stages"] for x in st]
+    batch.close()
+    for c in ctxs:
+        c.close()
+    return {"what": "64 float32 conduction problems, one RKL2 cycle each (dt/dt_E log-uniform 10..1e4)",
+            "cells": int(sum(c.n for c in ctxs)), "stages_min_max": [min(stages), max(stages)],
+            "point_stages": int(units), "tune": tune,
+            "batched_ms": ms_b, "batched_value": units / (ms_b / 1e3),
+            "separate_launches_ms": ms_s, "separate_value": units / (ms_s / 1e3),
+            "speedup_vs_separate": ms_s / ms_b, "unit": UNIT}
 
 
 def fp64_probe(pb, torch, g, d_tc, d_vi, d_u0, d_v0, wl, args, value32):

@@ -196,6 +196,42 @@ PB_API int pb_profile_enable(pb_ctx* ctx, int32_t on);
 /* Writes up to cap records (classes with at least one launch) and their number to *count. */
 PB_API int pb_profile_read(pb_ctx* ctx, pb_kernel_stat* out, int32_t cap, int32_t* count);
 
+/* ---- batched super time stepping ------------------------------------------------------------- */
+/* Many independent conduction problems (float32 contexts of any sizes) advanced by one cycle each,
+ * dt[p] with its own stage count, in ONE persistent kernel launched as a CUDA graph (a batched
+ * form of the Appendix A stage loop; the batching itself has no counterpart in the paper).
+ * Work items (problem, level, tile) are claimed in level-major order from a device counter; an
+ * item waits (bounded) for all tiles of its problem's previous level.  The tile schedule is set
+ * by pb_tune, chosen by pb_autotune from timed candidates. */
+typedef struct pb_batch pb_batch;
+
+typedef struct {
+    int32_t kchunk;         /* phi planes per tile (default 16)                              */
+    int32_t blocks_per_sm;  /* persistent blocks per SM (default 4)                          */
+    int32_t small_tiles;    /* 1: 16 x 16 (r, theta) tiles for grids with n_r <= 16 (default) */
+} pb_tune;
+
+PB_API void pb_tune_init(pb_tune* tune);
+
+/* ctxs: n float32 conduction contexts sharing one stream (not owned; they must outlive the
+ * batch; their y0 / stage buffers are the batch's scratch).  tune may be NULL. */
+PB_API int pb_batch_create(pb_ctx* const* ctxs, int32_t n, const pb_tune* tune, pb_batch** out);
+PB_API int pb_batch_destroy(pb_batch* batch);
+PB_API const char* pb_batch_last_error(const pb_batch* batch);
+
+/* Advances every u_devs[p] (device, float32, in place) over dts[p] with RKL2 or RKG2 (one cycle,
+ * no PTL), ordered after prior work on the contexts' stream; returns when done.
+ * per_problem (n entries, or NULL) receives cycles = 1 and the stage count. */
+PB_API int pb_batch_rkl2_advance(pb_batch* batch, void* const* u_devs, const double* dts, int32_t scheme,
+                                 pb_stats* per_problem);
+
+/* Times every candidate schedule (kchunk in {4, 8, 16, 32, 64} x blocks_per_sm in {2, 4, 6, 8}
+ * x small_tiles in {0, 1}) on scratch copies of the states (the caller's u_devs are not
+ * modified; this call allocates the copies), keeps the fastest in the batch and returns it
+ * and its time (ms) in *best_ms (may be NULL). */
+PB_API int pb_autotune(pb_batch* batch, void* const* u_devs, const double* dts, int32_t scheme, pb_tune* out,
+                       double* best_ms);
+
 /* ---- PTL without allocation ---------------------------------------------------------------- */
 /* PTL of a state (the same result as ptl_compute) for callers that cannot allocate device
  * memory: a host code that hands the solver a fixed, pre-sized device arena for a whole run, or

@@ -29,7 +29,8 @@ C_TC = (5.0 / 3.0 - 1.0) / 2.0
 EXPORTS = ("pb_advance_opts_init", "pb_status_string", "pb_last_error", "parabolic_setup",
            "parabolic_update", "parabolic_destroy", "parabolic_state_size", "parabolic_dt_explicit", "parabolic_apply",
            "ptl_compute", "rkl2_advance", "be_pcg_advance", "pb_profile_enable", "pb_profile_read",
-           "pb_ptl_noalloc")
+           "pb_ptl_noalloc", "pb_tune_init", "pb_batch_create", "pb_batch_destroy", "pb_batch_last_error",
+           "pb_batch_rkl2_advance", "pb_autotune")
 
 
 class PbGrid(ctypes.Structure):
@@ -61,6 +62,10 @@ class PbStats(ctypes.Structure):
 class PbKernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", c_int64), ("timed_launches", c_int64),
                 ("total_ms", c_double), ("bytes", c_double)]
+
+
+class PbTune(ctypes.Structure):
+    _fields_ = [("kchunk", c_int32), ("blocks_per_sm", c_int32), ("small_tiles", c_int32)]
 
 
 class ParabolicError(RuntimeError):
@@ -98,6 +103,17 @@ def load_library(path: str = LIB_PATH):
     lib.pb_ptl_noalloc.argtypes = [c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
                                    POINTER(c_double), POINTER(c_int64), POINTER(c_double), c_void_p]
     lib.pb_ptl_noalloc.restype = c_int32
+    lib.pb_tune_init.argtypes = [POINTER(PbTune)]
+    lib.pb_tune_init.restype = None
+    lib.pb_batch_create.argtypes = [POINTER(c_void_p), c_int32, POINTER(PbTune), POINTER(c_void_p)]
+    lib.pb_batch_destroy.argtypes = [c_void_p]
+    lib.pb_batch_last_error.argtypes = [c_void_p]
+    lib.pb_batch_last_error.restype = ctypes.c_char_p
+    lib.pb_batch_rkl2_advance.argtypes = [c_void_p, POINTER(c_void_p), POINTER(c_double), c_int32, POINTER(PbStats)]
+    lib.pb_autotune.argtypes = [c_void_p, POINTER(c_void_p), POINTER(c_double), c_int32, POINTER(PbTune),
+                                POINTER(c_double)]
+    for name in ("pb_batch_create", "pb_batch_destroy", "pb_batch_rkl2_advance", "pb_autotune"):
+        getattr(lib, name).restype = c_int32
     lib.pb_profile_enable.argtypes = [c_void_p, c_int32]
     lib.pb_profile_read.argtypes = [c_void_p, POINTER(PbKernelStat), c_int32, POINTER(c_int32)]
     for name in ("pb_profile_enable", "pb_profile_read", "parabolic_setup", "parabolic_update", "parabolic_destroy", "parabolic_state_size", "parabolic_dt_explicit",
@@ -344,5 +360,71 @@ def pb_profile_read(ctx: Context) -> list:
                  total_ms=buf[i].total_ms, bytes=buf[i].bytes) for i in range(n.value)]
 
 
-__all__ = ["pb_profile_enable", "pb_profile_read", "parabolic_setup", "parabolic_update", "parabolic_dt_explicit", "parabolic_apply", "ptl_compute", "rkl2_advance",
+class Batch:
+    """Many float32 conduction contexts advanced together by one persistent graph launch."""
+
+    def __init__(self, handle, ctxs):
+        self.handle = handle
+        self.ctxs = list(ctxs)   # kept alive: the batch uses their buffers
+
+    def close(self):
+        if self.handle:
+            load_library().pb_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _bcheck(status: int, handle):
+    if status != PB_OK:
+        lib = load_library()
+        raise ParabolicError(status, f"{lib.pb_status_string(status).decode()}: "
+                                     f"{lib.pb_batch_last_error(handle).decode()}")
+
+
+def pb_batch_create(ctxs, tune: dict | None = None) -> Batch:
+    lib = load_library()
+    arr = (c_void_p * len(ctxs))(*[c.handle for c in ctxs])
+    t = None
+    if tune is not None:
+        t = PbTune(int(tune["kchunk"]), int(tune["blocks_per_sm"]), int(tune["small_tiles"]))
+    h = c_void_p()
+    _bcheck(lib.pb_batch_create(arr, len(ctxs), byref(t) if t is not None else None, byref(h)), None)
+    return Batch(h, ctxs)
+
+
+def _uptrs(batch, us):
+    if len(us) != len(batch.ctxs):
+        raise ValueError("one state per context")
+    for c, u in zip(batch.ctxs, us):
+        _check_state(c, u)
+    return (c_void_p * len(us))(*[_ptr(u) for u in us])
+
+
+def pb_batch_rkl2_advance(batch: Batch, us, dts, scheme: str = "rkl2") -> list:
+    """Advances every us[p] in place over dts[p] (one cycle each) in one graph launch."""
+    lib = load_library()
+    n = len(us)
+    st = (PbStats * n)()
+    d = (c_double * n)(*[float(x) for x in dts])
+    _bcheck(lib.pb_batch_rkl2_advance(batch.handle, _uptrs(batch, us), d, SCHEMES[scheme], st), batch.handle)
+    return [dict(cycles=st[p].cycles, total_stages=st[p].total_stages) for p in range(n)]
+
+
+def pb_autotune(batch: Batch, us, dts, scheme: str = "rkl2"):
+    """Times the candidate schedules on copies of the states; returns (tune, best ms)."""
+    lib = load_library()
+    n = len(us)
+    d = (c_double * n)(*[float(x) for x in dts])
+    t = PbTune()
+    ms = c_double()
+    _bcheck(lib.pb_autotune(batch.handle, _uptrs(batch, us), d, SCHEMES[scheme], byref(t), byref(ms)), batch.handle)
+    return dict(kchunk=t.kchunk, blocks_per_sm=t.blocks_per_sm, small_tiles=t.small_tiles), ms.value
+
+
+__all__ = ["Batch", "pb_batch_create", "pb_batch_rkl2_advance", "pb_autotune", "pb_profile_enable", "pb_profile_read", "parabolic_setup", "parabolic_update", "parabolic_dt_explicit", "parabolic_apply", "ptl_compute", "rkl2_advance",
            "be_pcg_advance", "Context", "ParabolicError", "load_library", "EXPORTS"]

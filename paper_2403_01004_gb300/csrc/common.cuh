@@ -16,9 +16,12 @@ namespace pb {
 
 // ---- precision policies -----------------------------------------------------------------
 // S: state storage, C: coefficient storage, A: stencil / stage arithmetic.
-struct PolF64 { using S = double; using C = double; using A = double; static constexpr int id = PB_FP64; };
-struct PolF32 { using S = float; using C = float; using A = float; static constexpr int id = PB_FP32; };
-struct PolB16 { using S = __nv_bfloat16; using C = float; using A = float; static constexpr int id = PB_BF16_STORE; };
+// CG: operands may have been written earlier in the same launch (the batched persistent kernel),
+// so they are read through L2 (ld.global.cg) instead of the non-coherent read-only path.
+struct PolF64 { using S = double; using C = double; using A = double; static constexpr int id = PB_FP64; static constexpr bool CG = false; };
+struct PolF32 { using S = float; using C = float; using A = float; static constexpr int id = PB_FP32; static constexpr bool CG = false; };
+struct PolB16 { using S = __nv_bfloat16; using C = float; using A = float; static constexpr int id = PB_BF16_STORE; static constexpr bool CG = false; };
+struct PolF32CG : PolF32 { static constexpr bool CG = true; };
 
 template <typename T> __host__ __device__ __forceinline__ float to_f(T v);
 template <> __host__ __device__ __forceinline__ float to_f<float>(float v) { return v; }
@@ -34,6 +37,14 @@ template <> __device__ __forceinline__ __nv_bfloat16 ldg<__nv_bfloat16>(const __
     unsigned short s = __ldg(reinterpret_cast<const unsigned short*>(p));
     return __ushort_as_bfloat16(s);
 }
+
+template <typename T> __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ __nv_bfloat16 ldcg<__nv_bfloat16>(const __nv_bfloat16* p) {
+    unsigned short s = __ldcg(reinterpret_cast<const unsigned short*>(p));
+    return __ushort_as_bfloat16(s);
+}
+// Load of a state operand under policy P (read-only path, or L2 for in-launch producers).
+template <class P, typename T> __device__ __forceinline__ T ldx(const T* p) { return P::CG ? ldcg(p) : ldg(p); }
 
 // Packed 4-word coefficient record stored at every grid point [i,j,k]:
 //   conduction: {ahat_r, ahat_t, ahat_p} of corner [i,j,k] and the cell weight w of cell [i,j,k]

@@ -17,7 +17,7 @@ template <class P>
 struct LoadState {
     const typename P::S* u;
     __device__ void init() {}
-    __device__ typename P::A operator()(long long idx) const { return cvt<typename P::A>(ldg(u + idx)); }
+    __device__ typename P::A operator()(long long idx) const { return cvt<typename P::A>(ldx<P>(u + idx)); }
 };
 
 // PCG search direction p = z + beta p_old with z = D^-1 r, formed on the fly (halo included).
@@ -110,7 +110,7 @@ struct EpiStage {
     __device__ void init() {}
     __device__ bool skip() const { return false; }
     __device__ Pre prefetch(long long idx) const {
-        return Pre{KM2 ? cvt<A>(ldg(dkm2 + idx)) : A(0), cvt<A>(ldg(y0 + idx)), LAST ? cvt<A>(u0[idx]) : A(0)};
+        return Pre{KM2 ? cvt<A>(ldx<P>(dkm2 + idx)) : A(0), cvt<A>(ldx<P>(y0 + idx)), LAST ? cvt<A>(u0[idx]) : A(0)};
     }
     __device__ void apply(long long idx, A Au, A w, A dkm1, const Pre& p) {
         const A d = mu * dkm1 + nu * p.dkm2 + mdt * (w * Au) + ydt * p.y0;

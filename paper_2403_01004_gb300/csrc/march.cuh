@@ -56,45 +56,47 @@ __device__ __forceinline__ TileIdx decode_tile(const MarchGrid& g) {
 template <typename A> struct Quad { A e0, e1, e2, e3; };
 
 // ---------------------------------------------------------------------------------------------
-// Conduction march kernel.
+// Conduction march over one tile of TXv x TYv points (r, theta) and phi planes [k0, k1), run by a
+// block of at least TXv x TYv threads (tid = linear thread index; extra threads only help with
+// the halo and the extra corners).  Shared by the one-problem kernel below and the batched
+// persistent kernel.
 // Loader: A operator()(long long idx) const   (idx valid);   void init();
 // Epi: init(), skip(), Pre prefetch(idx), apply(idx, Au, w, center, pre), finish()
 // ---------------------------------------------------------------------------------------------
-template <class P, class Load, class Epi>
-__global__ void __launch_bounds__(NTHREADS)
-tc_march(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld_in, Epi ep_in) {
+template <class P, int TXv, int TYv>
+struct TileSmem {
+    typename P::A cell[2][TYv + 2][TXv + 2];
+    Quad<typename P::A> corn[2][TYv + 1][TXv + 1];
+};
+
+template <class P, int TXv, int TYv, class Load, class Epi>
+__device__ __forceinline__ void tc_tile(const CompGrid& cg, const TileIdx& t, const Coef4<typename P::C>* __restrict__ coef,
+                                        const Load& ld, Epi& ep, int tid, TileSmem<P, TXv, TYv>& sm) {
     using A = typename P::A;
-    __shared__ A cell[2][TY + 2][TX + 2];
-    __shared__ Quad<A> corn[2][TY + 1][TX + 1];
+    auto& cell = sm.cell;
+    auto& corn = sm.corn;
 
-    Epi ep = ep_in;
-    ep.init();
-    if (ep.skip()) return;
-    Load ld = ld_in;
-    ld.init();
-
-    const TileIdx t = decode_tile(g);
-    const CompGrid& cg = g.c[0];
     const int nr = cg.nr, nt = cg.nt, np = cg.np;
     const long long plane = (long long)nr * nt;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+    const int tx = tid % TXv, ty = tid / TXv;
+    const bool inb = tid < TXv * TYv;          // a point of the tile
     const int i = t.i0 + tx, j = t.j0 + ty;
-    const bool own = (i < nr) && (j < nt);
+    const bool own = inb && (i < nr) && (j < nt);
 
-    // halo slot handled by thread `tid` (84 halo cells for a 32 x 8 tile)
+    // halo slot handled by thread `tid` (2 (TXv + 2) + 2 TYv halo cells)
     int hi = -1, hj = -1;
-    if (tid < 2 * (TX + 2)) {
-        hi = tid % (TX + 2);
-        hj = tid < TX + 2 ? 0 : TY + 1;
-    } else if (tid < 2 * (TX + 2) + 2 * TY) {
-        const int q = tid - 2 * (TX + 2);
-        hi = q < TY ? 0 : TX + 1;
-        hj = 1 + (q % TY);
+    if (tid < 2 * (TXv + 2)) {
+        hi = tid % (TXv + 2);
+        hj = tid < TXv + 2 ? 0 : TYv + 1;
+    } else if (tid < 2 * (TXv + 2) + 2 * TYv) {
+        const int q = tid - 2 * (TXv + 2);
+        hi = q < TYv ? 0 : TXv + 1;
+        hj = 1 + (q % TYv);
     }
-    // extra corner handled by thread `tid` (41 corners on the low-r / low-theta edges)
+    // extra corner handled by thread `tid` (the TYv + 1 + TXv corners on the low-r / low-theta edges)
     int xci = -1, xcj = -1;
-    if (tid < TY + 1) { xci = 0; xcj = tid; }
-    else if (tid < TY + 1 + TX) { xci = tid - TY; xcj = 0; }
+    if (tid < TYv + 1) { xci = 0; xcj = tid; }
+    else if (tid < TYv + 1 + TXv) { xci = tid - TYv; xcj = 0; }
 
     auto fetch = [&](int gi, int gj, int kk) -> A {
         if (gi < 0 || gi >= nr || gj < 0 || gj >= nt) return A(0);
@@ -105,7 +107,7 @@ tc_march(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld_in,
         if (gi < 0 || gi >= nr || gj < 0 || gj >= nt) return Coef4<A>{A(0), A(0), A(0), A(0)};
         return load_coef<A, typename P::C>(coef + cg.offset + (long long)wrap_phi(kk, np) * plane + (long long)gj * nr + gi);
     };
-    // Corner (ci, cj) of the (TX+1) x (TY+1) corner grid from cell planes `pa` (k) and `pb` (k+1).
+    // Corner (ci, cj) of the (TXv+1) x (TYv+1) corner grid from cell planes `pa` (k) and `pb` (k+1).
     auto corner = [&](int cbuf, int pa, int pb, int ci, int cj, const Coef4<A>& c) {
         const A u000 = cell[pa][cj][ci], u100 = cell[pa][cj][ci + 1];
         const A u010 = cell[pa][cj + 1][ci], u110 = cell[pa][cj + 1][ci + 1];
@@ -124,23 +126,28 @@ tc_march(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld_in,
     };
 
     // prologue: cell planes k0-1, k0 and corner plane k0-1 into shared memory
-    cell[0][ty + 1][tx + 1] = fetch(i, j, t.k0 - 1);
-    if (hi >= 0) cell[0][hj][hi] = fetch(t.i0 - 1 + hi, t.j0 - 1 + hj, t.k0 - 1);
-    cell[1][ty + 1][tx + 1] = fetch(i, j, t.k0);
-    if (hi >= 0) cell[1][hj][hi] = fetch(t.i0 - 1 + hi, t.j0 - 1 + hj, t.k0);
+    if (inb) {
+        cell[0][ty + 1][tx + 1] = fetch(i, j, t.k0 - 1);
+        cell[1][ty + 1][tx + 1] = fetch(i, j, t.k0);
+    }
+    if (hi >= 0) {
+        cell[0][hj][hi] = fetch(t.i0 - 1 + hi, t.j0 - 1 + hj, t.k0 - 1);
+        cell[1][hj][hi] = fetch(t.i0 - 1 + hi, t.j0 - 1 + hj, t.k0);
+    }
     {
-        const Coef4<A> c0 = fetch_coef(tx + 1, ty + 1, t.k0 - 1);
-        Coef4<A> c1{A(0), A(0), A(0), A(0)};
+        Coef4<A> c0{A(0), A(0), A(0), A(0)}, c1{A(0), A(0), A(0), A(0)};
+        if (inb) c0 = fetch_coef(tx + 1, ty + 1, t.k0 - 1);
         if (xci >= 0) c1 = fetch_coef(xci, xcj, t.k0 - 1);
         __syncthreads();
-        corner(0, 0, 1, tx + 1, ty + 1, c0);
+        if (inb) corner(0, 0, 1, tx + 1, ty + 1, c0);
         if (xci >= 0) corner(0, 0, 1, xci, xcj, c1);
     }
     // register prefetch of the next plane: cell plane k+1, corner records of plane k, epilogue
     // operands of plane k
-    A nu_own = fetch(i, j, t.k0 + 1);
+    A nu_own = inb ? fetch(i, j, t.k0 + 1) : A(0);
     A nu_halo = hi >= 0 ? fetch(t.i0 - 1 + hi, t.j0 - 1 + hj, t.k0 + 1) : A(0);
-    Coef4<A> nc_own = fetch_coef(tx + 1, ty + 1, t.k0);
+    Coef4<A> nc_own{A(0), A(0), A(0), A(0)};
+    if (inb) nc_own = fetch_coef(tx + 1, ty + 1, t.k0);
     Coef4<A> nc_x{A(0), A(0), A(0), A(0)};
     if (xci >= 0) nc_x = fetch_coef(xci, xcj, t.k0);
     typename Epi::Pre npre{};
@@ -151,25 +158,25 @@ tc_march(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld_in,
     int kb = 0;   // corner buffer holding corner plane k-1
     for (int k = t.k0; k < t.k1; ++k) {
         const long long idx = cg.offset + (long long)k * plane + (long long)j * nr + i;
-        cell[cb ^ 1][ty + 1][tx + 1] = nu_own;
+        if (inb) cell[cb ^ 1][ty + 1][tx + 1] = nu_own;
         if (hi >= 0) cell[cb ^ 1][hj][hi] = nu_halo;
         const Coef4<A> c_own = nc_own, c_x = nc_x;
         const typename Epi::Pre pre = npre;
         if (k + 1 < t.k1) {
-            nu_own = fetch(i, j, k + 2);
+            if (inb) nu_own = fetch(i, j, k + 2);
             if (hi >= 0) nu_halo = fetch(t.i0 - 1 + hi, t.j0 - 1 + hj, k + 2);
-            nc_own = fetch_coef(tx + 1, ty + 1, k + 1);
+            if (inb) nc_own = fetch_coef(tx + 1, ty + 1, k + 1);
             if (xci >= 0) nc_x = fetch_coef(xci, xcj, k + 1);
             if (own) npre = ep.prefetch(idx + plane);
         }
         __syncthreads();
-        corner(kb ^ 1, cb, cb ^ 1, tx + 1, ty + 1, c_own);
+        if (inb) corner(kb ^ 1, cb, cb ^ 1, tx + 1, ty + 1, c_own);
         if (xci >= 0) corner(kb ^ 1, cb, cb ^ 1, xci, xcj, c_x);
-        const A center = cell[cb][ty + 1][tx + 1];
+        const A center = inb ? cell[cb][ty + 1][tx + 1] : A(0);
         __syncthreads();
         if (own) {
-            const Quad<A>(&Cp)[TY + 1][TX + 1] = corn[kb];       // corner plane k-1
-            const Quad<A>(&Cc)[TY + 1][TX + 1] = corn[kb ^ 1];   // corner plane k
+            const Quad<A>(&Cp)[TYv + 1][TXv + 1] = corn[kb];       // corner plane k-1
+            const Quad<A>(&Cc)[TYv + 1][TXv + 1] = corn[kb ^ 1];   // corner plane k
             const A sum = (Cp[ty][tx].e0 - Cc[ty + 1][tx + 1].e0) + (Cc[ty][tx].e1 - Cp[ty + 1][tx + 1].e1)
                         + (Cp[ty + 1][tx].e2 - Cc[ty][tx + 1].e2) + (Cc[ty + 1][tx].e3 - Cp[ty][tx + 1].e3);
             ep.apply(idx, -sum, c_own.w, center, pre);
@@ -177,6 +184,20 @@ tc_march(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld_in,
         cb ^= 1;
         kb ^= 1;
     }
+}
+
+// One-problem conduction march kernel (the register-prefetch path).
+template <class P, class Load, class Epi>
+__global__ void __launch_bounds__(NTHREADS)
+tc_march(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld_in, Epi ep_in) {
+    Epi ep = ep_in;
+    ep.init();
+    if (ep.skip()) return;
+    Load ld = ld_in;
+    ld.init();
+    const TileIdx t = decode_tile(g);
+    __shared__ TileSmem<P, TX, TY> sm;
+    tc_tile<P, TX, TY>(g.c[0], t, coef, ld, ep, threadIdx.x + TX * threadIdx.y, sm);
     ep.finish();
 }
 
