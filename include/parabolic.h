@@ -232,6 +232,53 @@ PB_API int pb_batch_rkl2_advance(pb_batch* batch, void* const* u_devs, const dou
 PB_API int pb_autotune(pb_batch* batch, void* const* u_devs, const double* dts, int32_t scheme, pb_tune* out,
                        double* best_ms);
 
+/* ---- learned PCG initial guess ---------------------------------------------------------------- */
+/* A small 3-D convolutional network (four 3 x 3 x 3 layers, 16 channels, ReLU between them,
+ * bfloat16 weights and activations, float32 accumulation) predicts the Backward Euler
+ * increment x - u^n from per-point features of the state; PCG (Sec. 3.1) starts from
+ * x0 = u^n + S y and still converges to the requested tolerance.  The paper has no network: it
+ * is an initial guess for the PC1 solve, trained on solves the library itself produces.
+ * Features (pb_guess_features), 6 of 16 channels: e/S with e = dt F(u) and S = rms(e);
+ * log10(1 + sigma) and sigma/(1 + sigma) with sigma = dt w |A_ii|; (u - mean u)/S;
+ * log10(w)/10; the normalised r index.  Tensors are [sample][n_phi][n_theta][n_r][16] bfloat16
+ * (features) and [sample][n_phi][n_theta][n_r] float32 (targets, outputs). */
+typedef struct pb_model pb_model;
+
+typedef struct {
+    int32_t steps;     /* optimisation steps                                               */
+    int32_t batch;     /* crops per step                                                   */
+    int32_t crop;      /* crop edge (points)                                               */
+    int32_t border;    /* loss excludes this many points at every crop face                */
+    double lr;         /* Adam learning rate                                               */
+    uint64_t seed;     /* crop sampling                                                    */
+} pb_train_opts;
+
+PB_API int pb_model_create(uint64_t seed, pb_model** out);
+PB_API int pb_model_destroy(pb_model* model);
+PB_API const char* pb_model_last_error(const pb_model* model);
+PB_API int pb_model_num_params(void);
+/* float32 parameters, per layer W[27][ci][co] (offset = 9 (dphi+1) + 3 (dtheta+1) + (dr+1)) then b[co] */
+PB_API int pb_model_get_params(const pb_model* model, float* host, int64_t cap);
+PB_API int pb_model_set_params(pb_model* model, const float* host, int64_t n);
+PB_API int pb_model_save(const pb_model* model, const char* path);
+PB_API int pb_model_load(pb_model* model, const char* path);
+/* Features of state u for a BE step of length dt (device, ctx precision, conduction or
+ * viscosity contexts with float64 / float32 storage), and S.  With x (the solved BE state) the
+ * training target (x - u)/S is written too (float32); x and target are both NULL or both set. */
+PB_API int pb_guess_features(pb_ctx* ctx, const void* u, double dt, const void* x, void* feats, void* target,
+                             double* scale);
+/* Network output for S_ samples of D x H x W feature points (wrap_d: periodic first axis). */
+PB_API int pb_model_forward(pb_model* model, const void* feats, int32_t S_, int32_t D, int32_t H, int32_t W,
+                            int32_t wrap_d, void* out, void* stream);
+/* Mean-squared-error loss over mask and its gradient (host float32, pb_model_num_params()). */
+PB_API int pb_model_grad(pb_model* model, const void* feats, const void* target, const void* mask, int32_t S_,
+                         int32_t D, int32_t H, int32_t W, double* loss, float* host_grad, void* stream);
+/* Adam training on random crops of nsamples equally sized samples (device feats / targets). */
+PB_API int pb_model_train(pb_model* model, const void* feats, const void* targets, int32_t nsamples, int32_t D,
+                          int32_t H, int32_t W, const pb_train_opts* opts, double* last_loss, void* stream);
+/* x0 = u + S model(features(u, dt)) for a conduction context (float64 / float32). */
+PB_API int learned_guess(pb_ctx* ctx, pb_model* model, const void* u, double dt, void* x0);
+
 /* ---- PTL without allocation ---------------------------------------------------------------- */
 /* PTL of a state (the same result as ptl_compute) for callers that cannot allocate device
  * memory: a host code that hands the solver a fixed, pre-sized device arena for a whole run, or

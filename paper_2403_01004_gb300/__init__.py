@@ -30,7 +30,9 @@ EXPORTS = ("pb_advance_opts_init", "pb_status_string", "pb_last_error", "parabol
            "parabolic_update", "parabolic_destroy", "parabolic_state_size", "parabolic_dt_explicit", "parabolic_apply",
            "ptl_compute", "rkl2_advance", "be_pcg_advance", "pb_profile_enable", "pb_profile_read",
            "pb_ptl_noalloc", "pb_tune_init", "pb_batch_create", "pb_batch_destroy", "pb_batch_last_error",
-           "pb_batch_rkl2_advance", "pb_autotune")
+           "pb_batch_rkl2_advance", "pb_autotune", "pb_model_create", "pb_model_destroy", "pb_model_last_error",
+           "pb_model_num_params", "pb_model_get_params", "pb_model_set_params", "pb_model_save", "pb_model_load",
+           "pb_guess_features", "pb_model_forward", "pb_model_grad", "pb_model_train", "learned_guess")
 
 
 class PbGrid(ctypes.Structure):
@@ -66,6 +68,11 @@ class PbKernelStat(ctypes.Structure):
 
 class PbTune(ctypes.Structure):
     _fields_ = [("kchunk", c_int32), ("blocks_per_sm", c_int32), ("small_tiles", c_int32)]
+
+
+class PbTrainOpts(ctypes.Structure):
+    _fields_ = [("steps", c_int32), ("batch", c_int32), ("crop", c_int32), ("border", c_int32),
+                ("lr", c_double), ("seed", ctypes.c_uint64)]
 
 
 class ParabolicError(RuntimeError):
@@ -113,6 +120,26 @@ def load_library(path: str = LIB_PATH):
     lib.pb_autotune.argtypes = [c_void_p, POINTER(c_void_p), POINTER(c_double), c_int32, POINTER(PbTune),
                                 POINTER(c_double)]
     for name in ("pb_batch_create", "pb_batch_destroy", "pb_batch_rkl2_advance", "pb_autotune"):
+        getattr(lib, name).restype = c_int32
+    lib.pb_model_create.argtypes = [ctypes.c_uint64, POINTER(c_void_p)]
+    lib.pb_model_destroy.argtypes = [c_void_p]
+    lib.pb_model_last_error.argtypes = [c_void_p]
+    lib.pb_model_last_error.restype = ctypes.c_char_p
+    lib.pb_model_num_params.argtypes = []
+    lib.pb_model_get_params.argtypes = [c_void_p, POINTER(ctypes.c_float), c_int64]
+    lib.pb_model_set_params.argtypes = [c_void_p, POINTER(ctypes.c_float), c_int64]
+    lib.pb_model_save.argtypes = [c_void_p, ctypes.c_char_p]
+    lib.pb_model_load.argtypes = [c_void_p, ctypes.c_char_p]
+    lib.pb_guess_features.argtypes = [c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p, POINTER(c_double)]
+    lib.pb_model_forward.argtypes = [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p]
+    lib.pb_model_grad.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32,
+                                  POINTER(c_double), POINTER(ctypes.c_float), c_void_p]
+    lib.pb_model_train.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32,
+                                   POINTER(PbTrainOpts), POINTER(c_double), c_void_p]
+    lib.learned_guess.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_void_p]
+    for name in ("pb_model_create", "pb_model_destroy", "pb_model_num_params", "pb_model_get_params",
+                 "pb_model_set_params", "pb_model_save", "pb_model_load", "pb_guess_features", "pb_model_forward",
+                 "pb_model_grad", "pb_model_train", "learned_guess"):
         getattr(lib, name).restype = c_int32
     lib.pb_profile_enable.argtypes = [c_void_p, c_int32]
     lib.pb_profile_read.argtypes = [c_void_p, POINTER(PbKernelStat), c_int32, POINTER(c_int32)]
@@ -426,5 +453,115 @@ def pb_autotune(batch: Batch, us, dts, scheme: str = "rkl2"):
     return dict(kchunk=t.kchunk, blocks_per_sm=t.blocks_per_sm, small_tiles=t.small_tiles), ms.value
 
 
-__all__ = ["Batch", "pb_batch_create", "pb_batch_rkl2_advance", "pb_autotune", "pb_profile_enable", "pb_profile_read", "parabolic_setup", "parabolic_update", "parabolic_dt_explicit", "parabolic_apply", "ptl_compute", "rkl2_advance",
+class Model:
+    """The learned-guess network (device parameters owned by the library)."""
+
+    def __init__(self, seed: int = 0):
+        lib = load_library()
+        h = c_void_p()
+        _mcheck(lib.pb_model_create(int(seed), byref(h)), None)
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            load_library().pb_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def num_params() -> int:
+        return load_library().pb_model_num_params()
+
+    def get_params(self):
+        import numpy as np
+        out = np.empty(self.num_params(), dtype=np.float32)
+        _mcheck(load_library().pb_model_get_params(self.handle, out.ctypes.data_as(POINTER(ctypes.c_float)), out.size),
+                self.handle)
+        return out
+
+    def set_params(self, params):
+        import numpy as np
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        _mcheck(load_library().pb_model_set_params(self.handle, a.ctypes.data_as(POINTER(ctypes.c_float)), a.size),
+                self.handle)
+
+    def save(self, path: str):
+        _mcheck(load_library().pb_model_save(self.handle, path.encode()), self.handle)
+
+    def load(self, path: str):
+        _mcheck(load_library().pb_model_load(self.handle, path.encode()), self.handle)
+
+
+def _mcheck(status: int, handle):
+    if status != PB_OK:
+        lib = load_library()
+        raise ParabolicError(status, f"{lib.pb_status_string(status).decode()}: "
+                                     f"{lib.pb_model_last_error(handle).decode()}")
+
+
+def pb_guess_features(ctx: Context, u, dt: float, x=None):
+    """(features [n_phi, n_theta, n_r, 16] bf16, target or None, S) for state u and BE step dt;
+    with the solved state x the training target (x - u)/S is returned too."""
+    torch = _torch()
+    _check_state(ctx, u)
+    feats = torch.empty(ctx.n * 16, dtype=torch.bfloat16, device=u.device)
+    target = torch.empty(ctx.n, dtype=torch.float32, device=u.device) if x is not None else None
+    S = c_double()
+    _check(load_library().pb_guess_features(ctx.handle, c_void_p(_ptr(u)), float(dt),
+                                            c_void_p(_ptr(x)) if x is not None else c_void_p(0), c_void_p(_ptr(feats)),
+                                            c_void_p(_ptr(target)) if target is not None else c_void_p(0), byref(S)),
+           ctx.handle)
+    return feats, target, S.value
+
+
+def pb_model_forward(model: Model, feats, shape, wrap_d: bool = False):
+    """Network output (float32) for feats of shape (samples, D, H, W) x 16 channels."""
+    torch = _torch()
+    S_, D, H, W = shape
+    out = torch.empty(S_ * D * H * W, dtype=torch.float32, device=feats.device)
+    _mcheck(load_library().pb_model_forward(model.handle, c_void_p(_ptr(feats)), S_, D, H, W, int(wrap_d),
+                                            c_void_p(_ptr(out)), c_void_p(_stream_handle(None))), model.handle)
+    return out
+
+
+def pb_model_grad(model: Model, feats, target, mask, shape):
+    """(loss, gradient wrt every parameter as a float32 numpy array)."""
+    import numpy as np
+    S_, D, H, W = shape
+    g = np.empty(Model.num_params(), dtype=np.float32)
+    L = c_double()
+    _mcheck(load_library().pb_model_grad(model.handle, c_void_p(_ptr(feats)), c_void_p(_ptr(target)),
+                                         c_void_p(_ptr(mask)), S_, D, H, W, byref(L),
+                                         g.ctypes.data_as(POINTER(ctypes.c_float)), c_void_p(_stream_handle(None))),
+            model.handle)
+    return L.value, g
+
+
+def pb_model_train(model: Model, feats, targets, shape, steps: int, batch: int = 8, crop: int = 24, border: int = 4,
+                   lr: float = 1e-3, seed: int = 0) -> float:
+    """Adam on random crops of the samples (feats (N, D, H, W, 16) bf16, targets (N, D, H, W))."""
+    N, D, H, W = shape
+    o = PbTrainOpts(int(steps), int(batch), int(crop), int(border), float(lr), int(seed))
+    L = c_double()
+    _mcheck(load_library().pb_model_train(model.handle, c_void_p(_ptr(feats)), c_void_p(_ptr(targets)), N, D, H, W,
+                                          byref(o), byref(L), c_void_p(_stream_handle(None))), model.handle)
+    return L.value
+
+
+def learned_guess(ctx: Context, model: Model, u, dt: float, x0=None):
+    """x0 = u + S model(features(u, dt)) for a conduction context."""
+    _check_state(ctx, u)
+    if x0 is None:
+        x0 = _torch().empty_like(u)
+    _check(load_library().learned_guess(ctx.handle, model.handle, c_void_p(_ptr(u)), float(dt), c_void_p(_ptr(x0))),
+           ctx.handle)
+    return x0
+
+
+__all__ = ["Model", "pb_guess_features", "pb_model_forward", "pb_model_grad", "pb_model_train", "learned_guess", "Batch", "pb_batch_create", "pb_batch_rkl2_advance", "pb_autotune", "pb_profile_enable", "pb_profile_read", "parabolic_setup", "parabolic_update", "parabolic_dt_explicit", "parabolic_apply", "ptl_compute", "rkl2_advance",
            "be_pcg_advance", "Context", "ParabolicError", "load_library", "EXPORTS"]

@@ -188,6 +188,21 @@ def visc_inputs(grid: Grid, seed: int, sigma: float = 0.1) -> ViscInputs:
     return ViscInputs(grid, v, rho, nu)
 
 
+def tc_random_inputs(grid: Grid, seed: int) -> TCInputs:
+    """Training profiles for the learned PCG guess: the conduction recipe with its shape
+    parameters drawn per sample -- temperature scale height H ~ U(1, 4), noise amplitude
+    ~ U(0.005, 0.05), density scale height ~ U(0.3, 1), dipole tilted uniformly on the sphere."""
+    rng = np.random.default_rng(seed)
+    H = rng.uniform(1.0, 4.0)
+    eps = rng.uniform(0.005, 0.05)
+    hn = rng.uniform(0.3, 1.0)
+    m = random_unit_vector(rng)
+    r = cell_r(grid)
+    T = (0.01 + 0.99 * np.exp(-(r - 1.0) / H)) * (1.0 + eps * rng.uniform(-1.0, 1.0, size=grid.shape))
+    n = np.exp(-(r - 1.0) / hn).copy()
+    return TCInputs(grid, np.ascontiguousarray(T), np.ascontiguousarray(n), dipole_corners(grid, m))
+
+
 # ---- workload recipes (sizes, stretch, dt ratios) ------------------------------------------
 
 WORKLOADS = {
