@@ -102,6 +102,8 @@ typedef struct {
     int32_t max_iter;         /* BE: PCG iteration cap per solve, default 100000            */
     int32_t fixed_iters;      /* BE: > 0 runs exactly this many iterations, no stop test    */
     int32_t check_every;      /* BE: iterations launched between host convergence checks   */
+    int32_t judge_guess;      /* BE with x0: 1 (default) starts from whichever of x0 and u^n
+                                 has the smaller initial residual ||b - S x||; 0 uses x0     */
 } pb_advance_opts;
 
 /* Statistics of an advance call (host struct).  The per-cycle arrays are optional caller-owned
@@ -121,6 +123,7 @@ typedef struct {
     int32_t* work_cycle;       /* STS stages s, or PCG iterations, per cycle                */
     double* dt_ptl_cycle;      /* PTL value before each cycle (NaN when not evaluated)      */
     int64_t* k_cycle;          /* argmax |F| location before each cycle (-1 when not)       */
+    int32_t guess_used;        /* BE: 1 if the first solve started from x0, 0 from u^n      */
 } pb_stats;
 
 /* Fills *opts with the defaults listed above. */

@@ -49,7 +49,7 @@ class PbAdvanceOpts(ctypes.Structure):
     _fields_ = [("scheme", c_int32), ("use_ptl", c_int32), ("max_cycles", c_int32),
                 ("ptl_floor", c_double), ("dt_cycles", POINTER(c_double)), ("n_forced", c_int32),
                 ("rtol", c_double), ("max_iter", c_int32), ("fixed_iters", c_int32),
-                ("check_every", c_int32)]
+                ("check_every", c_int32), ("judge_guess", c_int32)]
 
 
 class PbStats(ctypes.Structure):
@@ -58,7 +58,7 @@ class PbStats(ctypes.Structure):
                 ("fmax", c_double), ("k_index", c_int64), ("final_rel_residual", c_double),
                 ("cycle_capacity", c_int32), ("dt_cycle", POINTER(c_double)),
                 ("work_cycle", POINTER(c_int32)), ("dt_ptl_cycle", POINTER(c_double)),
-                ("k_cycle", POINTER(c_int64))]
+                ("k_cycle", POINTER(c_int64)), ("guess_used", c_int32)]
 
 
 class PbKernelStat(ctypes.Structure):
@@ -297,7 +297,7 @@ def ptl_compute(ctx: Context, u):
 
 
 def _opts(scheme="rkl2", use_ptl=True, max_cycles=0, ptl_floor=1.0, forced=None, rtol=1e-10,
-          max_iter=100000, fixed_iters=0, check_every=8):
+          max_iter=100000, fixed_iters=0, check_every=8, judge_guess=True):
     lib = load_library()
     o = PbAdvanceOpts()
     lib.pb_advance_opts_init(byref(o))
@@ -314,6 +314,7 @@ def _opts(scheme="rkl2", use_ptl=True, max_cycles=0, ptl_floor=1.0, forced=None,
     o.max_iter = int(max_iter)
     o.fixed_iters = int(fixed_iters)
     o.check_every = int(check_every)
+    o.judge_guess = 1 if judge_guess else 0
     return o, keep
 
 
@@ -338,7 +339,7 @@ class _StatsBuf:
                     dt_explicit=s.dt_explicit, last_dt_ptl=s.last_dt_ptl, fmax=s.fmax, k_index=s.k_index,
                     final_rel_residual=s.final_rel_residual, status_cycle=s.status_cycle,
                     dt_cycle=list(self.dt[:n]), work_cycle=list(self.work[:n]),
-                    dt_ptl_cycle=list(self.dtp[:n]), k_cycle=list(self.k[:n]))
+                    dt_ptl_cycle=list(self.dtp[:n]), k_cycle=list(self.k[:n]), guess_used=s.guess_used)
 
 
 def rkl2_advance(ctx: Context, u, dt: float, scheme: str = "rkl2", use_ptl: bool = True,
@@ -359,10 +360,13 @@ def rkl2_advance(ctx: Context, u, dt: float, scheme: str = "rkl2", use_ptl: bool
 def be_pcg_advance(ctx: Context, u, dt: float, use_ptl: bool = True, forced=None, rtol: float = 1e-10,
                    max_iter: int = 100000, fixed_iters: int = 0, x0=None, max_cycles: int = 0,
                    ptl_floor: float = 1.0, check_every: int = 8, stats_capacity: int = 4096,
-                   raise_on_error: bool = True) -> dict:
-    """Advances u in place over dt with Backward Euler + point-Jacobi PCG under PTL cycling."""
+                   raise_on_error: bool = True, judge_guess: bool = True) -> dict:
+    """Advances u in place over dt with Backward Euler + point-Jacobi PCG under PTL cycling.
+    With x0 (first cycle's initial guess) and judge_guess, the solve starts from whichever of
+    x0 and u has the smaller initial residual."""
     _check_state(ctx, u)
-    o, keep = _opts("rkl2", use_ptl, max_cycles, ptl_floor, forced, rtol, max_iter, fixed_iters, check_every)
+    o, keep = _opts("rkl2", use_ptl, max_cycles, ptl_floor, forced, rtol, max_iter, fixed_iters, check_every,
+                    judge_guess)
     sb = _StatsBuf(stats_capacity)
     x0p = c_void_p(_ptr(x0)) if x0 is not None else c_void_p(0)
     rc = load_library().be_pcg_advance(ctx.handle, c_void_p(_ptr(u)), float(dt), byref(o), x0p, byref(sb.st))

@@ -156,6 +156,7 @@ void stats_begin(pb_stats* st, const Ctx& c) {
     st->fmax = std::numeric_limits<double>::quiet_NaN();
     st->k_index = -1;
     st->final_rel_residual = std::numeric_limits<double>::quiet_NaN();
+    st->guess_used = 0;
 }
 
 void stats_cycle(pb_stats* st, double dt_c, int work, double dtp, long long k) {
@@ -231,6 +232,7 @@ void pb_advance_opts_init(pb_advance_opts* o) {
     o->max_iter = 100000;
     o->fixed_iters = 0;
     o->check_every = 8;
+    o->judge_guess = 1;
 }
 
 const char* pb_status_string(int s) {
@@ -511,15 +513,35 @@ int be_pcg_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, c
             }
             // u^n is kept in buf[0]: it is the right-hand side and the state restored on failure
             PB_CUDA_TRY(cudaMemcpyAsync(c.buf[0], u, bytes, cudaMemcpyDeviceToDevice, c.stream));
-            if (cycle == 0 && x0) PB_CUDA_TRY(cudaMemcpyAsync(u, x0, bytes, cudaMemcpyDeviceToDevice, c.stream));
             PcgScalars& hs = *c.h_pcg;
             std::memset(&hs, 0, sizeof(hs));
             hs.tol2 = o.rtol * o.rtol;
             hs.max_iter = o.max_iter;
             hs.fixed = o.fixed_iters > 0 ? o.fixed_iters : 0;
             hs.dt = dt_c;
-            PB_CUDA_TRY(cudaMemcpyAsync(c.d_pcg, &hs, sizeof(PcgScalars), cudaMemcpyHostToDevice, c.stream));
-            ops->pcg_init(c, u, c.buf[0], dt_c);
+            const PcgScalars hs0 = hs;
+            auto init = [&] {
+                *c.h_pcg = hs0;
+                PB_CUDA_TRY(cudaMemcpyAsync(c.d_pcg, c.h_pcg, sizeof(PcgScalars), cudaMemcpyHostToDevice, c.stream));
+                ops->pcg_init(c, u, c.buf[0], dt_c);
+                PB_CUDA_TRY(cudaMemcpyAsync(c.h_pcg, c.d_pcg, sizeof(PcgScalars), cudaMemcpyDeviceToHost, c.stream));
+                sync(c);
+                return c.h_pcg->rr;
+            };
+            if (cycle == 0 && x0) {
+                // the previous-step state is the fallback and the judge of a given guess
+                const double rr_prev = o.judge_guess ? init() : 0.0;
+                PB_CUDA_TRY(cudaMemcpyAsync(u, x0, bytes, cudaMemcpyDeviceToDevice, c.stream));
+                const double rr_x0 = init();
+                if (o.judge_guess && !(rr_x0 < rr_prev)) {
+                    PB_CUDA_TRY(cudaMemcpyAsync(u, c.buf[0], bytes, cudaMemcpyDeviceToDevice, c.stream));
+                    init();
+                } else if (st) {
+                    st->guess_used = 1;
+                }
+            } else {
+                init();
+            }
             int parity = 0;
             for (;;) {
                 PB_CUDA_TRY(cudaMemcpyAsync(c.h_pcg, c.d_pcg, sizeof(PcgScalars), cudaMemcpyDeviceToHost, c.stream));

@@ -46,13 +46,14 @@ def test_struct_layouts_match_header(tmp_path):
         "pb_grid": ("PbGrid", ["n_r", "n_theta", "n_phi", "r_face", "t_face"]),
         "pb_operator": ("PbOperator", ["kind", "C", "T0", "n", "B", "rho", "nu"]),
         "pb_advance_opts": ("PbAdvanceOpts", ["scheme", "use_ptl", "max_cycles", "ptl_floor", "dt_cycles",
-                                              "n_forced", "rtol", "max_iter", "fixed_iters", "check_every"]),
+                                              "n_forced", "rtol", "max_iter", "fixed_iters", "check_every",
+                                              "judge_guess"]),
         "pb_train_opts": ("PbTrainOpts", ["steps", "batch", "crop", "border", "lr", "seed"]),
         "pb_tune": ("PbTune", ["kchunk", "blocks_per_sm", "small_tiles"]),
         "pb_kernel_stat": ("PbKernelStat", ["name", "launches", "timed_launches", "total_ms", "bytes"]),
         "pb_stats": ("PbStats", ["cycles", "status_cycle", "total_stages", "total_iters", "dt_explicit",
                                  "last_dt_ptl", "fmax", "k_index", "final_rel_residual", "cycle_capacity",
-                                 "dt_cycle", "work_cycle", "dt_ptl_cycle", "k_cycle"]),
+                                 "dt_cycle", "work_cycle", "dt_ptl_cycle", "k_cycle", "guess_used"]),
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void) {"]
     for cname, (_, fl) in fields.items():
