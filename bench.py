@@ -55,6 +55,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-pcg", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-launch sub-benchmark")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-guess sub-benchmark")
     return ap.parse_args()
 
 
@@ -276,6 +277,8 @@ def run_ours(args):
         extra["pcg"] = pcg_probe(pb, torch, ctx_tc, d_tc, d_u0, u, wl)
     if not args.no_batch:
         extra["batched"] = batched_probe(pb, torch)
+    if not args.no_learned:
+        extra["learned_guess"] = learned_probe(pb, torch)
     if not args.no_fp64 and args.precision != "fp64":
         extra["fp64_plain"] = fp64_probe(pb, torch, g, d_tc, d_vi, d_u0, d_v0, wl, args, value)
     cpu = None
@@ -399,6 +402,53 @@ def batched_probe(pb, torch, reps=3):
             "batched_ms": ms_b, "batched_value": units / (ms_b / 1e3),
             "separate_launches_ms": ms_s, "separate_value": units / (ms_s / 1e3),
             "speedup_vs_separate": ms_s / ms_b, "unit": UNIT}
+
+
+def learned_probe(pb, torch):
+    """The learned-guess workload: BE conduction on the 192 x 192 x 384 shell at dt = 1e4 dt_E,
+    PCG (float64) to rtol 1e-10 from the zero, previous-step and learned (judged) guesses.  The
+    network is trained first on solves this library makes on 48 x 48 x 96 seeded random profiles."""
+    import synth
+    from paper_2403_01004_gb300 import learned
+    from synth import device
+    t0 = time.perf_counter()
+    feats, targ, gen_iters = learned.generate(64, shape=(48, 48, 96), seed=7)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    model, loss = learned.train(feats, targ, steps=1000, batch=8, crop=24, border=4, lr=2e-3, seed=1)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del feats, targ
+    wl = synth.WORKLOADS["shell192"]
+    g = synth.make_grid(wl["n_r"], wl["n_t"], wl["n_p"], wl["q"])
+    inp = synth.tc_inputs(g, wl["seed"])
+    ctx = pb.parabolic_setup(g.r_face, g.t_face, g.n_phi, "tc", device.tc_fields(inp), "fp64")
+    u = torch.from_numpy(inp.T.reshape(-1)).cuda()
+    dt = wl["ratio"] * pb.parabolic_dt_explicit(ctx)
+    out = {}
+    for name in ("zero", "previous", "learned_raw", "learned_judged"):
+        x = u.clone()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        x0 = None
+        if name == "zero":
+            x0 = torch.zeros_like(u)
+        elif name.startswith("learned"):
+            x0 = pb.learned_guess(ctx, model, u, dt)
+        st = pb.be_pcg_advance(ctx, x, dt, use_ptl=False, rtol=1e-10, x0=x0, judge_guess=(name == "learned_judged"))
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = {"iterations": st["total_iters"], "ms": e0.elapsed_time(e1),
+                     "rel_residual": st["final_rel_residual"], "started_from_guess": bool(st["guess_used"])}
+    ctx.close()
+    model.close()
+    return {"what": "BE + PC1 PCG (float64, rtol 1e-10), 192x192x384 shell, dt = 1e4 dt_E, one solve per guess",
+            "training": {"samples": 64, "sample_grid": "48x48x96", "solve_iterations": gen_iters,
+                         "generate_s": round(t_gen, 2), "steps": 1000, "train_s": round(t_train, 2),
+                         "last_batch_loss": loss},
+            **out}
 
 
 def fp64_probe(pb, torch, g, d_tc, d_vi, d_u0, d_v0, wl, args, value32):
