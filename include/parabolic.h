@@ -104,6 +104,9 @@ typedef struct {
     int32_t check_every;      /* BE: iterations launched between host convergence checks   */
     int32_t judge_guess;      /* BE with x0: 1 (default) starts from whichever of x0 and u^n
                                  has the smaller initial residual ||b - S x||; 0 uses x0     */
+    int32_t mixed_precision;  /* BE on a PB_FP64 context: 1 solves by iterative refinement --
+                                 float64 residuals, float32 PCG corrections (default 0)      */
+    double inner_rtol;        /* relative residual of each float32 correction (default 1e-3) */
 } pb_advance_opts;
 
 /* Statistics of an advance call (host struct).  The per-cycle arrays are optional caller-owned

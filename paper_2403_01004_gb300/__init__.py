@@ -49,7 +49,8 @@ class PbAdvanceOpts(ctypes.Structure):
     _fields_ = [("scheme", c_int32), ("use_ptl", c_int32), ("max_cycles", c_int32),
                 ("ptl_floor", c_double), ("dt_cycles", POINTER(c_double)), ("n_forced", c_int32),
                 ("rtol", c_double), ("max_iter", c_int32), ("fixed_iters", c_int32),
-                ("check_every", c_int32), ("judge_guess", c_int32)]
+                ("check_every", c_int32), ("judge_guess", c_int32), ("mixed_precision", c_int32),
+                ("inner_rtol", c_double)]
 
 
 class PbStats(ctypes.Structure):
@@ -297,7 +298,7 @@ def ptl_compute(ctx: Context, u):
 
 
 def _opts(scheme="rkl2", use_ptl=True, max_cycles=0, ptl_floor=1.0, forced=None, rtol=1e-10,
-          max_iter=100000, fixed_iters=0, check_every=8, judge_guess=True):
+          max_iter=100000, fixed_iters=0, check_every=8, judge_guess=True, mixed=False, inner_rtol=1e-3):
     lib = load_library()
     o = PbAdvanceOpts()
     lib.pb_advance_opts_init(byref(o))
@@ -315,6 +316,8 @@ def _opts(scheme="rkl2", use_ptl=True, max_cycles=0, ptl_floor=1.0, forced=None,
     o.fixed_iters = int(fixed_iters)
     o.check_every = int(check_every)
     o.judge_guess = 1 if judge_guess else 0
+    o.mixed_precision = 1 if mixed else 0
+    o.inner_rtol = float(inner_rtol)
     return o, keep
 
 
@@ -360,13 +363,14 @@ def rkl2_advance(ctx: Context, u, dt: float, scheme: str = "rkl2", use_ptl: bool
 def be_pcg_advance(ctx: Context, u, dt: float, use_ptl: bool = True, forced=None, rtol: float = 1e-10,
                    max_iter: int = 100000, fixed_iters: int = 0, x0=None, max_cycles: int = 0,
                    ptl_floor: float = 1.0, check_every: int = 8, stats_capacity: int = 4096,
-                   raise_on_error: bool = True, judge_guess: bool = True) -> dict:
+                   raise_on_error: bool = True, judge_guess: bool = True, mixed: bool = False,
+                   inner_rtol: float = 1e-3) -> dict:
     """Advances u in place over dt with Backward Euler + point-Jacobi PCG under PTL cycling.
     With x0 (first cycle's initial guess) and judge_guess, the solve starts from whichever of
     x0 and u has the smaller initial residual."""
     _check_state(ctx, u)
     o, keep = _opts("rkl2", use_ptl, max_cycles, ptl_floor, forced, rtol, max_iter, fixed_iters, check_every,
-                    judge_guess)
+                    judge_guess, mixed, inner_rtol)
     sb = _StatsBuf(stats_capacity)
     x0p = c_void_p(_ptr(x0)) if x0 is not None else c_void_p(0)
     rc = load_library().be_pcg_advance(ctx.handle, c_void_p(_ptr(u)), float(dt), byref(o), x0p, byref(sb.st))

@@ -79,6 +79,8 @@ void build_grid(Ctx& c) {
 void free_ctx(Ctx& c) {
     cudaStreamSynchronize(c.stream);
     c.prof.release();
+    free_shadow(c.shadow);
+    c.shadow = nullptr;
     void* ptrs[] = {c.coef, c.coef_be, c.coef64, c.adiag, c.y0, c.buf[0], c.buf[1], c.buf[2], c.r, c.p[0],
                     c.p[1], c.q, c.dinv, c.partials, c.counter, c.d_ptl, c.d_pcg, c.d_scalar, c.d_flag, c.d_err};
     for (void* p : ptrs)
@@ -139,6 +141,7 @@ pb_advance_opts resolve(const pb_advance_opts* o) {
     if (!(r.rtol > 0.0)) r.rtol = 1e-10;
     if (r.max_iter < 0) r.max_iter = 100000;
     if (r.check_every <= 0) r.check_every = 8;
+    if (!(r.inner_rtol > 0.0) || !(r.inner_rtol < 1.0)) r.inner_rtol = 1e-3;
     if (r.scheme != PB_RKL2 && r.scheme != PB_RKG2) throw Error{PB_EINVAL, "unknown scheme"};
     if (r.dt_cycles == nullptr) r.n_forced = 0;
     if (r.n_forced < 0) throw Error{PB_EINVAL, "n_forced < 0"};
@@ -233,6 +236,8 @@ void pb_advance_opts_init(pb_advance_opts* o) {
     o->fixed_iters = 0;
     o->check_every = 8;
     o->judge_guess = 1;
+    o->mixed_precision = 0;
+    o->inner_rtol = 1e-3;
 }
 
 const char* pb_status_string(int s) {
@@ -542,14 +547,42 @@ int be_pcg_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, c
             } else {
                 init();
             }
-            int parity = 0;
-            for (;;) {
-                PB_CUDA_TRY(cudaMemcpyAsync(c.h_pcg, c.d_pcg, sizeof(PcgScalars), cudaMemcpyDeviceToHost, c.stream));
-                sync(c);
-                if (c.h_pcg->done) break;
-                for (int m = 0; m < o.check_every; ++m) {
-                    ops->pcg_iter(c, u, parity, dt_c);
-                    parity ^= 1;
+            if (o.mixed_precision && c.prec == PB_FP64 && o.fixed_iters <= 0) {
+                // iterative refinement: float64 residual (the set-up pass above) and float32
+                // corrections until r.r <= rtol^2 b.b
+                long long inner = 0;
+                int refine = 0;
+                for (;;) {
+                    const PcgScalars now = *c.h_pcg;
+                    if (now.done == 2) break;
+                    if (now.rr <= now.tol2 * now.bb) {
+                        c.h_pcg->done = 1;
+                        break;
+                    }
+                    if (refine >= 64 || inner >= o.max_iter) {
+                        c.h_pcg->done = 3;
+                        break;
+                    }
+                    int status = 0;
+                    inner += mixed_inner(c, u, dt_c, o.inner_rtol, o.max_iter - inner, o.check_every, &status);
+                    ++refine;
+                    if (status == 2) {
+                        c.h_pcg->done = 2;
+                        break;
+                    }
+                    init();
+                }
+                c.h_pcg->iter = inner;
+            } else {
+                int parity = 0;
+                for (;;) {
+                    PB_CUDA_TRY(cudaMemcpyAsync(c.h_pcg, c.d_pcg, sizeof(PcgScalars), cudaMemcpyDeviceToHost, c.stream));
+                    sync(c);
+                    if (c.h_pcg->done) break;
+                    for (int m = 0; m < o.check_every; ++m) {
+                        ops->pcg_iter(c, u, parity, dt_c);
+                        parity ^= 1;
+                    }
                 }
             }
             const PcgScalars r = *c.h_pcg;

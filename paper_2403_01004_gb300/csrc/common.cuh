@@ -138,6 +138,7 @@ struct Ctx {
     double* s64 = nullptr;         // float64 scratch [n]: kappa, then diag(A)
     double* geo[16] = {};          // device copies of the face / point coordinate arrays
     Prof prof;
+    struct Ctx* shadow = nullptr;  // float32 shadow for mixed-precision BE (float64 contexts)
     std::string err;
     int sm_count = 0;
 };

@@ -47,4 +47,9 @@ void setup_visc(Ctx& c, const pb_operator& op, Coef4<double>* rec, double* dt_e)
 
 int reduce_blocks(const Ctx& c);   // grid size of the element-wise reduction kernels
 
+// mixed-precision Backward Euler (mixed.cu)
+Ctx& mixed_shadow(Ctx& c);
+void free_shadow(Ctx* s);
+long long mixed_inner(Ctx& c, void* x, double dt, double inner_rtol, long long max_iter, int check_every, int* status);
+
 }  // namespace pb

@@ -193,3 +193,26 @@ def test_tma_and_fallback_kernels_agree(prec, monkeypatch):
         pb.rkl2_advance(ctx, ud, dt, use_ptl=True)
         outs.append(to_host(ud))
     assert rel_l2(outs[0], outs[1]) <= {"fp64": 1e-14, "fp32": 1e-6, "bf16": 1e-2}[prec]
+
+
+@pytest.mark.parametrize("kind", ["tc", "visc"])
+def test_be_mixed_precision_refinement(kind):
+    """Float64 context, float32 PCG corrections with float64 residuals: the true residual meets
+    rtol and the state agrees with the oracle's converged BE to the solver tolerance.  The
+    oracle's PTL schedule is replayed on both sides: the solves differ at the 1e-11 level, which
+    can move a (discontinuous) PTL decision."""
+    import paper_2403_01004_gb300 as pb
+    g, inp, op, u = tc_problem(32, 32, 64) if kind == "tc" else visc_problem(24, 20, 16)
+    ctx = gpu_ctx(kind, g, inp, "fp64")
+    dt = 100.0 * op.dt_explicit()
+    _, log = be_advance(op, u, dt, use_ptl=True, rtol=1e-12)
+    uo, _ = be_advance(op, u, dt, forced=log.dt_c, rtol=1e-12)
+    ud = to_dev(u, ctx)
+    st = pb.be_pcg_advance(ctx, ud, dt, forced=log.dt_c, rtol=1e-10, mixed=True)
+    assert st["cycles"] == log.cycles
+    assert st["final_rel_residual"] <= 1e-10
+    assert rel_l2(to_host(ud), uo) <= 1e-8
+    # and driven by its own PTL decisions it still meets the tolerance in every cycle
+    ud = to_dev(u, ctx)
+    st = pb.be_pcg_advance(ctx, ud, dt, use_ptl=True, rtol=1e-10, mixed=True)
+    assert st["final_rel_residual"] <= 1e-10 and abs(st["cycles"] - log.cycles) <= 2
