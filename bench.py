@@ -274,7 +274,7 @@ def run_ours(args):
 
     extra = {}
     if not args.no_pcg:
-        extra["pcg"] = pcg_probe(pb, torch, ctx_tc, d_tc, d_u0, u, wl)
+        extra["pcg"] = pcg_probe(pb, torch, g, d_tc, d_u0, wl)
     if not args.no_batch:
         extra["batched"] = batched_probe(pb, torch)
     if not args.no_learned:
@@ -335,24 +335,29 @@ def traffic_for(kernel: str, args):
     return e
 
 
-def pcg_probe(pb, torch, ctx_tc, d_tc, d_u0, u, wl):
-    """Backward Euler + PCG on the same conduction problem: one cycle of dt = 1e3 dt_E solved to
-    rtol 1e-10 (float32 vectors reach their own floor first, so a fixed iteration count is timed)."""
-    pb.parabolic_update(ctx_tc, d_tc)
-    dt = wl["ratio"] * pb.parabolic_dt_explicit(ctx_tc)
-    u.copy_(d_u0)
-    pb.be_pcg_advance(ctx_tc, u, dt, use_ptl=False, fixed_iters=10)
-    iters = 50
-    u.copy_(d_u0)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    pb.be_pcg_advance(ctx_tc, u, dt, use_ptl=False, fixed_iters=iters)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    return {"what": "BE + point-Jacobi PCG, conduction, dt = 1e3 dt_E, 50 iterations (fixed)",
-            "ms_per_iteration": ms / iters, "point_iterations_per_s": ctx_tc.n * iters / (ms / 1e3)}
+def pcg_probe(pb, torch, g, d_tc, d_u0, wl):
+    """Backward Euler + point-Jacobi PCG on the same conduction problem, float64 state, to
+    rtol 1e-10: one cycle of dt = 1e3 dt_E with plain float64 PCG and with mixed precision
+    (float64 residuals, float32 corrections), and the whole step under PTL cycling (mixed)."""
+    ctx = pb.parabolic_setup(g.r_face, g.t_face, g.n_phi, "tc", d_tc, "fp64")
+    u0 = d_u0.to(torch.float64)
+    dt = wl["ratio"] * pb.parabolic_dt_explicit(ctx)
+    out = {"what": "BE + PC1 PCG, shell256 conduction, float64 state, rtol 1e-10"}
+    for name, kw in (("one_cycle_fp64", dict(use_ptl=False)), ("one_cycle_mixed", dict(use_ptl=False, mixed=True)),
+                     ("ptl_step_mixed", dict(use_ptl=True, mixed=True))):
+        u = u0.clone()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st = pb.be_pcg_advance(ctx, u, dt, rtol=1e-10, **kw)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"ms": ms, "cycles": st["cycles"], "iterations": st["total_iters"],
+                     "rel_residual": st["final_rel_residual"],
+                     "point_iterations_per_s": ctx.n * st["total_iters"] / (ms / 1e3)}
+    ctx.close()
+    return out
 
 
 def batched_probe(pb, torch, reps=3):
@@ -437,14 +442,15 @@ def learned_probe(pb, torch):
             x0 = torch.zeros_like(u)
         elif name.startswith("learned"):
             x0 = pb.learned_guess(ctx, model, u, dt)
-        st = pb.be_pcg_advance(ctx, x, dt, use_ptl=False, rtol=1e-10, x0=x0, judge_guess=(name == "learned_judged"))
+        st = pb.be_pcg_advance(ctx, x, dt, use_ptl=False, rtol=1e-10, x0=x0, judge_guess=(name == "learned_judged"),
+                               mixed=True)
         e1.record()
         torch.cuda.synchronize()
         out[name] = {"iterations": st["total_iters"], "ms": e0.elapsed_time(e1),
                      "rel_residual": st["final_rel_residual"], "started_from_guess": bool(st["guess_used"])}
     ctx.close()
     model.close()
-    return {"what": "BE + PC1 PCG (float64, rtol 1e-10), 192x192x384 shell, dt = 1e4 dt_E, one solve per guess",
+    return {"what": "BE + PC1 PCG (mixed precision, rtol 1e-10), 192x192x384 shell, dt = 1e4 dt_E, one solve per guess",
             "training": {"samples": 64, "sample_grid": "48x48x96", "solve_iterations": gen_iters,
                          "generate_s": round(t_gen, 2), "steps": 1000, "train_s": round(t_train, 2),
                          "last_batch_loss": loss},

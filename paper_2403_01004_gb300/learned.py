@@ -29,7 +29,7 @@ def generate(n_samples: int, shape=(48, 48, 96), q: float = 1.05, ratio: float =
         u = torch.from_numpy(inp.T.reshape(-1)).cuda()
         dt = ratio * parabolic_dt_explicit(ctx)
         x = u.clone()
-        st = be_pcg_advance(ctx, x, dt, use_ptl=False, rtol=rtol)
+        st = be_pcg_advance(ctx, x, dt, use_ptl=False, rtol=rtol, mixed=True)
         iters += st["total_iters"]
         f, t, _ = pb_guess_features(ctx, u, dt, x)
         feats[i].copy_(f.view(n_p, n_t, n_r, 16))
