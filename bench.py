@@ -56,6 +56,7 @@ def parse_args():
     ap.add_argument("--no-pcg", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-launch sub-benchmark")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-guess sub-benchmark")
+    ap.add_argument("--no-rkg2", action="store_true", help="skip the RKG2 comparison step")
     return ap.parse_args()
 
 
@@ -126,6 +127,21 @@ class ClockSampler:
         reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+# ---- multi-rank aggregation ----------------------------------------------------------------------
+def reduce_timing(units: float, ms: float, device="cuda"):
+    """Whole-job units (sum over ranks) and the slowest rank's time (max over ranks); each rank
+    runs an independent replica, so no data crosses ranks except these two numbers."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return units, ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()), float(t.item())
 
 
 # ---- our implementation --------------------------------------------------------------------
@@ -215,12 +231,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         ms = ev0.elapsed_time(ev1)
+        units, ms = reduce_timing(units, ms)
         if world > 1:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-            if world > 1:
-                torch.distributed.barrier()
+            torch.distributed.barrier()
         return units, ms, wall
 
     for _ in range(args.warmup):
@@ -237,7 +250,7 @@ def run_ours(args):
     pb.pb_profile_enable(ctx_tc, False)
     pb.pb_profile_enable(ctx_v, False)
     step_stats = {k: dict(cycles=v_["cycles"], stages=v_["total_stages"]) for k, v_ in stats.items()}
-    value = world * units / (ms / 1e3)
+    value = units / (ms / 1e3)
     launches = sum(p["launches"] for p in prof)
 
     e2e = None
@@ -246,7 +259,7 @@ def run_ours(args):
         units_e, ms_e, _ = timed(e2e_step, args.steps)
         h2d = sum(t.numel() * t.element_size() for t in [h_tc["T0"], h_tc["n"], *h_tc["B"], *h_vi["rho"], *h_vi["nu"], h_u, h_v])
         d2h = out_u.numel() * out_u.element_size() + out_v.numel() * out_v.element_size()
-        e2e = {"value": world * units_e / (ms_e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": units_e / (ms_e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e / args.steps}
 
     # dominant kernel class of the timed region and its roofline against measured HBM bandwidth
@@ -273,6 +286,16 @@ def run_ours(args):
                 if p["total_ms"] > 0 else None} for p in sorted(prof, key=lambda p: -p["total_ms"])]
 
     extra = {}
+    if not args.no_rkg2 and args.scheme == "rkl2":
+        # the paper's own scheme (Appendix A) on the same step: same kernels, its coefficients
+        # and odd stage counts; its stronger high-mode damping changes the PTL schedule
+        prev = args.scheme
+        args.scheme = "rkg2"
+        step(d_tc, d_vi, d_u0, d_v0)
+        units_g, ms_g, _ = timed(lambda: step(d_tc, d_vi, d_u0, d_v0), 1)
+        args.scheme = prev
+        extra["rkg2_step"] = {"value": units_g / (ms_g / 1e3), "unit": UNIT, "ms_per_step": ms_g,
+                              "step": {k: dict(cycles=v_["cycles"], stages=v_["total_stages"]) for k, v_ in stats.items()}}
     if not args.no_pcg:
         extra["pcg"] = pcg_probe(pb, torch, g, d_tc, d_u0, wl)
     if not args.no_batch:

@@ -22,7 +22,10 @@ Balsara & Aslam, restated here from its stability polynomial R_s(z) = a_s + b_s 
 
 Both stage-count rules are evaluated as integer inequalities ((s^2+s-2) >= 4r and
 (s+4)(s-1) >= 6r, the squared forms of the square-root formulas) so that exact-integer ratios do
-not round up.  s >= 2 is needed for w (undefined at s = 1); RKG2 is then raised to odd s >= 3.
+not round up, and with r taken as r (1 - 1e-12): a ratio within rounding of a stage-count
+boundary (a cycle length equal to dt_E, say) takes the smaller count instead of a count decided
+by the last bit of dt_E.  s >= 2 is needed for w (undefined at s = 1); RKG2 is then raised to odd
+s >= 3.
 """
 from __future__ import annotations
 
@@ -32,6 +35,7 @@ import math
 import numpy as np
 
 MAX_STAGES = 1 << 20
+TIE = 1.0 - 1e-12      # ratios within 1e-12 of a boundary take the smaller stage count
 
 
 @dataclasses.dataclass
@@ -46,6 +50,7 @@ class STSCoefficients:
 def rkl2_stages(r: float) -> int:
     if not (r >= 0.0) or math.isinf(r):
         raise ValueError("dt/dt_E must be finite and >= 0")
+    r = r * TIE
     s = max(2, int(math.ceil((math.sqrt(9.0 + 16.0 * r) - 1.0) / 2.0)))
     while s > 2 and (s - 1) * (s - 1) + (s - 1) - 2 >= 4.0 * r:
         s -= 1
@@ -59,6 +64,7 @@ def rkl2_stages(r: float) -> int:
 def rkg2_stages(r: float) -> int:
     if not (r >= 0.0) or math.isinf(r):
         raise ValueError("dt/dt_E must be finite and >= 0")
+    r = r * TIE
     s = max(2, int(math.ceil(0.5 * math.sqrt(25.0 + 24.0 * r) - 1.5)))
     while s > 2 and (s - 1 + 4) * (s - 1 - 1) >= 6.0 * r:
         s -= 1

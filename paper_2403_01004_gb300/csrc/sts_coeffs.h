@@ -28,7 +28,13 @@ struct Sts {
     std::vector<double> mu, nu, mut, gt;
 };
 
+// Ratios within 1e-12 (relative) of a stage-count boundary take the smaller count, so that a
+// cycle length equal to a boundary up to rounding (e.g. dt_c = dt_E) does not decide s by the
+// last bit of dt_E.
+inline constexpr double kStageTie = 1.0 - 1e-12;
+
 inline long long stages_rkl2(double r) {
+    r *= kStageTie;
     long long s = std::max(2LL, (long long)std::ceil((std::sqrt(9.0 + 16.0 * r) - 1.0) / 2.0));
     while (s > 2 && (double)((s - 1) * (s - 1) + (s - 1) - 2) >= 4.0 * r) --s;
     while ((double)(s * s + s - 2) < 4.0 * r) ++s;
@@ -36,6 +42,7 @@ inline long long stages_rkl2(double r) {
 }
 
 inline long long stages_rkg2(double r) {
+    r *= kStageTie;
     long long s = std::max(2LL, (long long)std::ceil(0.5 * std::sqrt(25.0 + 24.0 * r) - 1.5));
     while (s > 2 && (double)((s + 3) * (s - 2)) >= 6.0 * r) --s;
     while ((double)((s + 4) * (s - 1)) < 6.0 * r) ++s;

@@ -54,15 +54,22 @@ def test_stage_count_inequalities_sweep():
     """s is the smallest admissible count: the stability bound holds at s and fails at s-1."""
     for r in np.concatenate([np.linspace(0.01, 50, 997), np.logspace(0, 6, 500)]):
         s = rkl2_stages(r)
-        assert (s * s + s - 2) / 4.0 >= r
+        assert (s * s + s - 2) / 4.0 >= r * (1 - 1e-12)
         assert s == 2 or ((s - 1) ** 2 + (s - 1) - 2) / 4.0 < r
         g = rkg2_stages(r)
         assert g % 2 == 1 and g >= 3
-        assert (g + 4) * (g - 1) / 6.0 >= r
+        assert (g + 4) * (g - 1) / 6.0 >= r * (1 - 1e-12)
         # the paper's ceil formula, then odd
         ref = max(2, math.ceil(0.5 * math.sqrt(25 + 24 * r) - 1.5))
         ref += (ref % 2 == 0)
         assert g == ref or abs(0.5 * math.sqrt(25 + 24 * r) - 1.5 - round(0.5 * math.sqrt(25 + 24 * r) - 1.5)) < 1e-9
+
+
+def test_stage_count_ties_take_the_smaller_count():
+    """A ratio equal to a boundary up to rounding gives the boundary's count on both sides."""
+    for r, s in ((1.0, 2), (1.0 + 2.2e-16, 2), (10.0 * (1 + 4e-16), 6), (1.0 + 1e-9, 3)):
+        assert rkl2_stages(r) == s, r
+    assert rkg2_stages(1000.0 * (1 + 3e-16)) == 77
 
 
 def _stability_scalar(co, z):
