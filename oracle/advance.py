@@ -4,7 +4,9 @@ full step dt in cycles, the PTL being re-evaluated from the current state before
 Reading fixed by the project (the paper gives no formula for the cycle length): with t_rem the
 time still to cover and the limit floored at the explicit step, dt_L = max(dt_PTL, floor dt_E),
 n = ceil(t_rem / dt_L) (n = 1 when dt_L >= t_rem), the next cycle has length dt_c = t_rem / n,
-and the loop stops once t_rem <= 1e-12 dt.  The floor (default 1, in units of dt_E) keeps the
+and the loop stops once t_rem <= 1e-12 dt.  As for the stage counts, a quotient t_rem / dt_L
+within 1e-12 (relative) of an integer takes the smaller n, so that the cycle count is not
+decided by the last bit of dt_E when dt is a whole multiple of it.  The floor (default 1, in units of dt_E) keeps the
 loop from cycling more finely than the explicit stability limit, which Sec. 2 names as the costly
 extreme the PTL is meant to improve on: taken literally, a cycle of length dt_PTL drives the
 neighbour difference at k towards zero, so the next dt_PTL collapses and the loop need not end.
@@ -21,7 +23,7 @@ import numpy as np
 
 from .pcg import be_solve
 from .ptl import ptl
-from .sts import SCHEMES, sts_step
+from .sts import SCHEMES, TIE, sts_step
 
 
 class MaxCyclesError(RuntimeError):
@@ -63,7 +65,8 @@ def _cycles(op, u, dt, use_ptl, forced, max_cycles, log, needs_F_always, floor):
             if use_ptl:
                 dtp, k, _ = ptl(op, u, F)
                 dtl = max(dtp, floor * dtE)
-                n = 1.0 if dtl >= t_rem else math.ceil(t_rem / dtl)
+                q = t_rem / dtl * TIE
+                n = 1.0 if q <= 1.0 else math.ceil(q)
                 dt_c = t_rem / n
             else:
                 dtp, k = math.nan, -1

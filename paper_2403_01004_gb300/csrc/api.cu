@@ -200,6 +200,16 @@ void update_coefficients(Ctx& c, const pb_operator& op) {
     if (!(c.dt_e > 0.0) || std::isinf(c.dt_e)) throw Error{PB_ENONFINITE, "dt_E is not a positive finite number"};
 }
 
+// The next cycle's length (Sec. 2): n = ceil(t_rem / max(dt_PTL, floor)) cycles remain and the
+// next one has t_rem / n; a quotient within 1e-12 of an integer takes the smaller n (the same
+// rule as the stage counts), so a dt that is a whole multiple of dt_E gives that many cycles.
+double cycle_length(double t_rem, double dt_ptl, double floor_dt) {
+    const double dtl = std::max(dt_ptl, floor_dt);
+    const double q = t_rem / dtl * kStageTie;
+    const double n = q <= 1.0 ? 1.0 : std::ceil(q);
+    return t_rem / n;
+}
+
 // Runs the PTL pass on u (y0 = F(u) in c.y0) and returns the result (host).
 PtlResult run_ptl(Ctx& c, Ops* ops, const void* u) {
     ops->y0_pass(c, u, c.y0, true, nullptr, 0.0);
@@ -443,9 +453,7 @@ int rkl2_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, pb_
                     dtp = r.dt_ptl;
                     kk = r.k;
                     if (st) { st->last_dt_ptl = r.dt_ptl; st->fmax = r.fmax; st->k_index = r.k; }
-                    const double dtl = std::max(dtp, o.ptl_floor * c.dt_e);
-                    const double n = dtl >= t_rem ? 1.0 : std::ceil(t_rem / dtl);
-                    dt_c = t_rem / n;
+                    dt_c = cycle_length(t_rem, dtp, o.ptl_floor * c.dt_e);
                     y0_done = true;
                 } else {
                     dt_c = t_rem;
@@ -509,9 +517,7 @@ int be_pcg_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, c
                     dtp = r.dt_ptl;
                     kk = r.k;
                     if (st) { st->last_dt_ptl = r.dt_ptl; st->fmax = r.fmax; st->k_index = r.k; }
-                    const double dtl = std::max(dtp, o.ptl_floor * c.dt_e);
-                    const double n = dtl >= t_rem ? 1.0 : std::ceil(t_rem / dtl);
-                    dt_c = t_rem / n;
+                    dt_c = cycle_length(t_rem, dtp, o.ptl_floor * c.dt_e);
                 } else {
                     dt_c = t_rem;
                 }
