@@ -280,10 +280,7 @@ def run_ours(args):
                 "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "alg_bytes_per_launch": per_launch_bytes,
                 "ms_per_launch": round(per_launch_ms, 4)}
-    kernels = [{"name": p["name"], "launches": p["launches"], "ms": round(p["total_ms"], 3),
-                "share": round(p["total_ms"] / max(1e-9, sum(q["total_ms"] for q in prof)), 4),
-                "GB/s": round(p["bytes"] / max(1, p["launches"]) / (p["total_ms"] / max(1, p["timed_launches"]) / 1e3) / 1e9, 1)
-                if p["total_ms"] > 0 else None} for p in sorted(prof, key=lambda p: -p["total_ms"])]
+    kernels = kernel_table(prof)
 
     extra = {}
     if not args.no_rkg2 and args.scheme == "rkl2":
@@ -326,6 +323,15 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def kernel_table(prof):
+    """Per kernel class: launches, event-timed total, share, and algorithmic GB/s per launch."""
+    total = max(1e-9, sum(q["total_ms"] for q in prof))
+    return [{"name": p["name"], "launches": p["launches"], "ms": round(p["total_ms"], 3),
+             "share": round(p["total_ms"] / total, 4),
+             "GB/s": round(p["bytes"] / max(1, p["launches"]) / (p["total_ms"] / max(1, p["timed_launches"]) / 1e3) / 1e9, 1)
+             if p["total_ms"] > 0 else None} for p in sorted(prof, key=lambda p: -p["total_ms"])]
 
 
 KERNEL_SOURCES = ("common.cuh", "prof.h", "reduce.cuh", "march.cuh", "march_tma.cuh", "tma.cuh",
@@ -379,6 +385,13 @@ def pcg_probe(pb, torch, g, d_tc, d_u0, wl):
         out[name] = {"ms": ms, "cycles": st["cycles"], "iterations": st["total_iters"],
                      "rel_residual": st["final_rel_residual"],
                      "point_iterations_per_s": ctx.n * st["total_iters"] / (ms / 1e3)}
+        # per kernel class (a separate, event-timed run of the same solve)
+        u = u0.clone()
+        pb.pb_profile_enable(ctx, True)
+        pb.be_pcg_advance(ctx, u, dt, rtol=1e-10, **kw)
+        torch.cuda.synchronize()
+        out[name]["kernels"] = kernel_table(pb.pb_profile_read(ctx))
+        pb.pb_profile_enable(ctx, False)
     ctx.close()
     return out
 

@@ -230,12 +230,14 @@ struct EpiPcgSpmv {
     A dt;
     int done;
     double acc[1];
+    static constexpr int NC = 0;     // point operands delivered by the TMA kernel
     __device__ void init() {
         acc[0] = 0.0;
         done = sc->done;
     }
     __device__ bool skip() const { return done != 0; }
     __device__ Pre prefetch(long long) const { return {}; }
+    __device__ void apply_c(long long idx, A Au, A m, A pv, A, A, A) { apply(idx, Au, m, pv, Pre{}); }
     __device__ void apply(long long idx, A Au, A m, A pv, const Pre&) {
         const S ps = cvt<S>(pv);
         const S qs = cvt<S>(m * pv - dt * Au);
@@ -270,27 +272,9 @@ __global__ void stage1_kernel(long long n, const typename P::S* y0, typename P::
         d1[t] = cvt<typename P::S>(a * cvt<A>(y0[t]));
 }
 
-// PCG update: x += alpha p, r -= alpha q, z = D^-1 r, sums <r, z> and <r, r>; the last block
-// applies the stopping test (r.r <= rtol^2 b.b after the update) and forms beta.
-template <class P>
-__global__ void __launch_bounds__(256)
-pcg_update_kernel(long long n, typename P::S* x, typename P::S* r, const typename P::S* p,
-                  const typename P::S* q, const typename P::S* dinv, PcgScalars* sc,
-                  double* part, unsigned int* counter) {
-    using A = typename P::A;
-    using S = typename P::S;
-    if (sc->done) return;
-    const A alpha = (A)sc->alpha;
-    double acc[2] = {0.0, 0.0};
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-        x[t] = cvt<S>(cvt<A>(x[t]) + alpha * cvt<A>(p[t]));
-        const S rs = cvt<S>(cvt<A>(r[t]) - alpha * cvt<A>(q[t]));
-        r[t] = rs;
-        const A ra = cvt<A>(rs);
-        const double z = (double)cvt<A>(cvt<S>(cvt<A>(dinv[t]) * ra));
-        acc[0] += (double)ra * z;
-        acc[1] += (double)ra * (double)ra;
-    }
+// Block partials of <r, z> and <r, r>; the last block applies the stopping test (r.r <= rtol^2 b.b
+// after the update) and forms beta.
+__device__ inline void pcg_update_finish(double (&acc)[2], PcgScalars* sc, double* part, unsigned int* counter) {
     block_sum<2>(acc);
     if (threadIdx.x == 0) {
         part[blockIdx.x * 4 + 0] = acc[0];
@@ -317,6 +301,68 @@ pcg_update_kernel(long long n, typename P::S* x, typename P::S* r, const typenam
             *counter = 0u;
         }
     }
+}
+
+// PCG update: x += alpha p, r -= alpha q, z = D^-1 r, sums <r, z> and <r, r>.
+template <class P>
+__global__ void __launch_bounds__(256)
+pcg_update_kernel(long long n, typename P::S* x, typename P::S* r, const typename P::S* p,
+                  const typename P::S* q, const typename P::S* dinv, PcgScalars* sc,
+                  double* part, unsigned int* counter) {
+    using A = typename P::A;
+    using S = typename P::S;
+    if (sc->done) return;
+    const A alpha = (A)sc->alpha;
+    double acc[2] = {0.0, 0.0};
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        x[t] = cvt<S>(cvt<A>(x[t]) + alpha * cvt<A>(p[t]));
+        const S rs = cvt<S>(cvt<A>(r[t]) - alpha * cvt<A>(q[t]));
+        r[t] = rs;
+        const A ra = cvt<A>(rs);
+        const double z = (double)cvt<A>(cvt<S>(cvt<A>(dinv[t]) * ra));
+        acc[0] += (double)ra * z;
+        acc[1] += (double)ra * (double)ra;
+    }
+    pcg_update_finish(acc, sc, part, counter);
+}
+
+// The same update for float32 state, four points per step through 16-byte accesses (all five
+// arrays 16-byte aligned).  The dot products sum each group of four in float and add the group
+// sums in double: GB300 issues float64 arithmetic at a small fraction of its float32 rate, and
+// double arithmetic on every point would bound this pass instead of HBM.
+static __global__ void __launch_bounds__(256)
+pcg_update_f32x4_kernel(long long n, float* x, float* r, const float* p, const float* q, const float* dinv,
+                        PcgScalars* sc, double* part, unsigned int* counter) {
+    if (sc->done) return;
+    const float alpha = (float)sc->alpha;
+    double acc[2] = {0.0, 0.0};
+    const long long n4 = n >> 2;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (long long t = t0; t < n4; t += stride) {
+        float4 xv = reinterpret_cast<const float4*>(x)[t];
+        float4 rv = reinterpret_cast<const float4*>(r)[t];
+        const float4 pv = __ldg(reinterpret_cast<const float4*>(p) + t);
+        const float4 qv = __ldg(reinterpret_cast<const float4*>(q) + t);
+        const float4 dv = __ldg(reinterpret_cast<const float4*>(dinv) + t);
+        xv.x += alpha * pv.x; xv.y += alpha * pv.y; xv.z += alpha * pv.z; xv.w += alpha * pv.w;
+        rv.x -= alpha * qv.x; rv.y -= alpha * qv.y; rv.z -= alpha * qv.z; rv.w -= alpha * qv.w;
+        reinterpret_cast<float4*>(x)[t] = xv;
+        reinterpret_cast<float4*>(r)[t] = rv;
+        const float rz = rv.x * (dv.x * rv.x) + rv.y * (dv.y * rv.y) + rv.z * (dv.z * rv.z) + rv.w * (dv.w * rv.w);
+        const float rr = rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
+        acc[0] += (double)rz;
+        acc[1] += (double)rr;
+    }
+    const long long tt = 4 * n4 + t0;          // the last n mod 4 points
+    if (tt < n) {
+        x[tt] += alpha * p[tt];
+        const float rs = r[tt] - alpha * q[tt];
+        r[tt] = rs;
+        acc[0] += (double)(rs * (dinv[tt] * rs));
+        acc[1] += (double)(rs * rs);
+    }
+    pcg_update_finish(acc, sc, part, counter);
 }
 
 // PTL (Eq. 5) at k = argmax |F| over the block partials; one block.

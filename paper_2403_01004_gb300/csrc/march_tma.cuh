@@ -12,6 +12,11 @@
 // field, corners k+1/2, point operands) and k-k0+2 (plane k+1: field).  Every wait is bounded:
 // if a copy never lands the block records the failure in *err, waits (bounded) for its other
 // copies and returns.
+//
+// The field is either one array (PlainField) or, for the PCG product, assembled per plane from
+// several arrays (PcgField): once a slot has landed the block forms the field on the whole halo
+// box into a buffer of that slot that only ordinary stores write, so the TMA destinations are
+// never written by the threads.
 #pragma once
 
 #include "march.cuh"
@@ -25,7 +30,41 @@ constexpr int kSlots = 4;
 
 __host__ __device__ constexpr int align128(int b) { return (b + 127) & ~127; }
 
-template <class P, int NC>
+// The field of the conduction product: one array read as it is.
+template <class P>
+struct PlainField {
+    static constexpr int NF = 1;
+    __device__ void init() {}
+    __device__ void combine(unsigned char*, int, int, typename P::S*) const {}
+};
+
+// The PCG search direction p = z + beta p_old with z = D^-1 r rounded to the state precision,
+// formed from the arrays r, D^-1 and p_old exactly as the register path does (Sec. 3.1 PCG).
+template <class P>
+struct PcgField {
+    using A = typename P::A;
+    using S = typename P::S;
+    static constexpr int NF = 3;
+    const PcgScalars* sc;
+    A beta;
+    int first;
+    __device__ void init() {
+        beta = (A)sc->beta;
+        first = sc->first;
+    }
+    // src: NF arrays of n points, each at `pitch` bytes from the previous; dst: n points
+    __device__ void combine(unsigned char* base, int pitch, int n, S* dst) const {
+        const S* r = reinterpret_cast<const S*>(base);
+        const S* di = reinterpret_cast<const S*>(base + pitch);
+        const S* po = reinterpret_cast<const S*>(base + 2 * pitch);
+        for (int e = threadIdx.x + TX * threadIdx.y; e < n; e += NTHREADS) {
+            const A z = cvt<A>(cvt<S>(cvt<A>(di[e]) * cvt<A>(r[e])));
+            dst[e] = cvt<S>(first ? z : z + beta * cvt<A>(po[e]));
+        }
+    }
+};
+
+template <class P, int NC, int NF = 1>
 struct TmaLayout {
     using S = typename P::S;
     using C = typename P::C;
@@ -33,13 +72,16 @@ struct TmaLayout {
     static constexpr int HX = HaloPad<S>::value;
     static constexpr int BXW = TX + 2 * HX;                              // halo box width (points)
     static constexpr int U_BYTES = (TY + 2) * BXW * (int)sizeof(S);
+    static constexpr int U_PITCH = align128(U_BYTES);
     static constexpr int C_BYTES = (TY + 1) * (TX + 1) * 4 * (int)sizeof(C);
     static constexpr int E_BYTES = TY * TX * (int)sizeof(S);
     static constexpr int U_OFF = 0;
-    static constexpr int C_OFF = align128(U_BYTES);
+    static constexpr int C_OFF = NF * U_PITCH;
     static constexpr int E_OFF = C_OFF + align128(C_BYTES);
-    static constexpr int SLOT = E_OFF + NC * align128(E_BYTES);
-    static constexpr int TX_BYTES = U_BYTES + C_BYTES + NC * E_BYTES;    // bytes a slot's copies deliver
+    static constexpr int P_OFF = E_OFF + NC * align128(E_BYTES);         // assembled field (NF > 1)
+    static constexpr int FIELD_OFF = NF > 1 ? P_OFF : U_OFF;
+    static constexpr int SLOT = P_OFF + (NF > 1 ? U_PITCH : 0);
+    static constexpr int TX_BYTES = NF * U_BYTES + C_BYTES + NC * E_BYTES;   // bytes a slot's copies deliver
     static constexpr int CW = TX + 2;                                    // corner row pitch
     static constexpr int CORN_OFF = kSlots * SLOT;
     static constexpr int CORN_BYTES = 2 * 4 * (TY + 1) * CW * (int)sizeof(A);
@@ -47,13 +89,13 @@ struct TmaLayout {
     static constexpr int TOTAL = BAR_OFF + kSlots * 8 + 16;
 };
 
-template <class P, class Epi>
+template <class P, class Epi, class Field = PlainField<P>>
 __global__ void __launch_bounds__(NTHREADS)
-tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* err) {
+tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* err, Field fld = Field{}) {
     using S = typename P::S;
     using C = typename P::C;
     using A = typename P::A;
-    using L = TmaLayout<P, Epi::NC>;
+    using L = TmaLayout<P, Epi::NC, Field::NF>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // TMA destinations are kept 128-byte aligned (the launch adds 128 bytes of slack)
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -64,6 +106,7 @@ tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* 
     Epi ep = ep_in;
     ep.init();
     if (ep.skip()) return;
+    fld.init();
 
     const TileIdx t = decode_tile(g);
     const CompGrid& cg = g.c[0];
@@ -85,7 +128,8 @@ tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* 
         int z = t.k0 - 1 + q;
         z = z < 0 ? z + np : (z >= np ? z - np : z);
         mbar_expect_tx(bar, L::TX_BYTES);
-        tma_load_3d(s + L::U_OFF, &maps.halo, t.i0 - L::HX, t.j0 - 1, z, bar);
+#pragma unroll
+        for (int f = 0; f < Field::NF; ++f) tma_load_3d(s + L::U_OFF + f * L::U_PITCH, &maps.halo[f], t.i0 - L::HX, t.j0 - 1, z, bar);
         tma_load_4d(s + L::C_OFF, &maps.coef, 0, t.i0 - 1, t.j0 - 1, z, bar);
 #pragma unroll
         for (int a = 0; a < Epi::NC; ++a) tma_load_3d(s + L::E_OFF + a * align128(L::E_BYTES), &maps.cen[a], t.i0, t.j0, z, bar);
@@ -94,7 +138,12 @@ tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* 
     auto wait = [&](int q) -> bool {
         if (!mbar_wait(bars + (q % kSlots), (q / kSlots) & 1)) *abort_flag = 1;
         __syncthreads();
-        return *abort_flag == 0;
+        if (*abort_flag != 0) return false;
+        if constexpr (Field::NF > 1) {
+            fld.combine(slot(q) + L::U_OFF, L::U_PITCH, (TY + 2) * L::BXW, reinterpret_cast<S*>(slot(q) + L::P_OFF));
+            __syncthreads();
+        }
+        return true;
     };
     auto bail = [&](int issued, int waited) {
         if (tid == 0) {
@@ -104,7 +153,7 @@ tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* 
         __syncthreads();
     };
     auto U = [&](int q, int yy, int xx) -> A {
-        return cvt<A>(reinterpret_cast<const S*>(slot(q) + L::U_OFF)[yy * L::BXW + xx]);
+        return cvt<A>(reinterpret_cast<const S*>(slot(q) + L::FIELD_OFF)[yy * L::BXW + xx]);
     };
     // corner (ci, cj) of plane z = k0-1+q from field slots q (plane z) and q+1 (plane z+1)
     auto corner = [&](int cbuf, int q, int ci, int cj) -> A {

@@ -89,7 +89,8 @@ Ctx& mixed_shadow(Ctx& c) {
         s->n = c.n;
         s->dt_e = c.dt_e;
         s->sm_count = c.sm_count;
-        s->use_tma = false;
+        s->use_tma = c.use_tma;
+        s->d_err = c.d_err;                          // shared: the parent's sync reports a timeout
         const size_t n = (size_t)c.n;
         s->coef = dalloc(n * sizeof(Coef4<float>));
         s->coef_be = dalloc(n * sizeof(Coef4<float>));
@@ -124,6 +125,7 @@ void free_shadow(Ctx* s) {
     for (void* q : p)
         if (q) cudaFree(q);
     if (s->h_pcg) cudaFreeHost(s->h_pcg);
+    s->prof.release();
     delete s;
 }
 
@@ -140,12 +142,16 @@ long long mixed_inner(Ctx& c, void* x, double dt, double inner_rtol, long long m
     h.dt = dt;
     PB_CUDA_TRY(cudaMemcpyAsync(s.d_pcg, &h, sizeof(h), cudaMemcpyHostToDevice, s.stream));
     const int blocks = reduce_blocks(s);
+    s.prof.on = c.prof.on;
+    {
+    KScope ks(s.prof, s.stream, K_PCG32_REFINE, (double)s.n * (8 + 16 + 4 + 3 * 4));
     init_rhs_kernel<<<blocks, 256, 0, s.stream>>>(s.n, static_cast<const double*>(c.r),
                                                    static_cast<const Coef4<float>*>(s.coef_be),
                                                    static_cast<const float*>(s.adiag), dt, static_cast<float*>(s.r),
                                                    static_cast<float*>(s.dinv), static_cast<float*>(s.y0), s.d_pcg,
                                                    static_cast<double*>(s.partials), s.counter);
     PB_CUDA_TRY(cudaGetLastError());
+    }
     int parity = 0;
     Ops* ops = ops_f32();
     for (;;) {
@@ -160,10 +166,16 @@ long long mixed_inner(Ctx& c, void* x, double dt, double inner_rtol, long long m
     const PcgScalars r = *s.h_pcg;
     *status = r.done == 1 ? 0 : r.done;
     if (r.done != 2) {
+        KScope ks(s.prof, s.stream, K_PCG32_REFINE, (double)s.n * (8 + 4 + 8));
         add_correction_kernel<<<reduce_blocks(c), 256, 0, c.stream>>>(c.n, static_cast<double*>(x),
                                                                       static_cast<const float*>(s.y0));
         PB_CUDA_TRY(cudaGetLastError());
     }
+    PB_CUDA_TRY(cudaStreamSynchronize(s.stream));
+    s.prof.harvest();
+    c.prof.absorb(s.prof, K_PCG_SPMV, K_PCG32_SPMV);
+    c.prof.absorb(s.prof, K_PCG_UPDATE, K_PCG32_UPDATE);
+    c.prof.absorb(s.prof, K_PCG32_REFINE, K_PCG32_REFINE);
     return r.iter;
 }
 

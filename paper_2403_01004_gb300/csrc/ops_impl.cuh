@@ -1,6 +1,9 @@
 // Launchers for one precision policy P; included by ops_f64.cu / ops_f32.cu / ops_b16.cu.
 #pragma once
 
+#include <cstdint>
+#include <type_traits>
+
 #include "epilogues.cuh"
 #include "launch.h"
 #include "march.cuh"
@@ -33,7 +36,7 @@ class OpsImpl : public Ops {
             using L = TmaLayout<P, Epi::NC>;
             const CompGrid& g = c.grid.c[0];
             TmaMaps maps;
-            bool ok = tma_state_map(&maps.halo, field, sizeof(S), g.nr, g.nt, g.np, L::BXW, TY + 2) &&
+            bool ok = tma_state_map(&maps.halo[0], field, sizeof(S), g.nr, g.nt, g.np, L::BXW, TY + 2) &&
                       tma_coef_map(&maps.coef, c.coef, sizeof(C), g.nr, g.nt, g.np, TX + 1, TY + 1);
             for (int a = 0; ok && a < Epi::NC; ++a)
                 ok = tma_state_map(&maps.cen[a], cen[a], sizeof(S), g.nr, g.nt, g.np, TX, TY);
@@ -50,6 +53,31 @@ class OpsImpl : public Ops {
             }
         }
         march(c, c.coef, LoadState<P>{static_cast<const S*>(field)}, ep);
+    }
+
+    // PCG product q = S p through the TMA kernel, p assembled on chip from r, D^-1 and p_old;
+    // false when the arrays cannot be described by tensor maps (the caller then uses tc_march).
+    static bool pcg_spmv_tma(Ctx& c, const S* pold, const EpiPcgSpmv<P>& ep) {
+        if (c.kind != PB_TC_ANISO || !c.use_tma) return false;
+        using Fld = PcgField<P>;
+        using L = TmaLayout<P, 0, Fld::NF>;
+        const CompGrid& g = c.grid.c[0];
+        TmaMaps maps;
+        const void* f[3] = {c.r, c.dinv, pold};
+        bool ok = tma_coef_map(&maps.coef, c.coef_be, sizeof(C), g.nr, g.nt, g.np, TX + 1, TY + 1);
+        for (int a = 0; ok && a < 3; ++a) ok = tma_state_map(&maps.halo[a], f[a], sizeof(S), g.nr, g.nt, g.np, L::BXW, TY + 2);
+        if (!ok) return false;
+        static bool attr = false;
+        const int smem = L::TOTAL + 128;
+        if (!attr) {
+            PB_CUDA_TRY(cudaFuncSetAttribute(tc_march_tma<P, EpiPcgSpmv<P>, Fld>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            attr = true;
+        }
+        tc_march_tma<P, EpiPcgSpmv<P>, Fld><<<c.grid.nblocks, dim3(TX, TY), smem, c.stream>>>(c.grid, maps, ep, c.d_err,
+                                                                                             Fld{c.d_pcg, A(0), 0});
+        PB_CUDA_TRY(cudaGetLastError());
+        return true;
     }
 
 public:
@@ -156,13 +184,26 @@ public:
                          c.grid.nblocks, (A)dt};
         {
             KScope ks(c.prof, c.stream, K_PCG_SPMV, nb(c, 5, 4));
-            march(c, c.coef_be, ld, ep);
+            if (!pcg_spmv_tma(c, pold, ep)) march(c, c.coef_be, ld, ep);
         }
         const int blocks = reduce_blocks(c);
         KScope ks(c.prof, c.stream, K_PCG_UPDATE, nb(c, 7, 0));
-        pcg_update_kernel<P><<<blocks, 256, 0, c.stream>>>(c.n, static_cast<S*>(x), static_cast<S*>(c.r), pnew,
-                                                           static_cast<const S*>(c.q), static_cast<const S*>(c.dinv),
-                                                           c.d_pcg, static_cast<double*>(c.partials), c.counter);
+        bool vec = false;
+        if constexpr (std::is_same<S, float>::value && std::is_same<A, float>::value) {
+            const uintptr_t a = reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(c.r) |
+                                reinterpret_cast<uintptr_t>(pnew) | reinterpret_cast<uintptr_t>(c.q) |
+                                reinterpret_cast<uintptr_t>(c.dinv);
+            if ((a & 15) == 0) {
+                pcg_update_f32x4_kernel<<<blocks, 256, 0, c.stream>>>(
+                    c.n, static_cast<float*>(x), static_cast<float*>(c.r), pnew, static_cast<const float*>(c.q),
+                    static_cast<const float*>(c.dinv), c.d_pcg, static_cast<double*>(c.partials), c.counter);
+                vec = true;
+            }
+        }
+        if (!vec)
+            pcg_update_kernel<P><<<blocks, 256, 0, c.stream>>>(c.n, static_cast<S*>(x), static_cast<S*>(c.r), pnew,
+                                                               static_cast<const S*>(c.q), static_cast<const S*>(c.dinv),
+                                                               c.d_pcg, static_cast<double*>(c.partials), c.counter);
         PB_CUDA_TRY(cudaGetLastError());
     }
 

@@ -20,12 +20,16 @@ enum KClass {
     K_PCG_SPMV,
     K_PCG_UPDATE,
     K_SETUP,
+    K_PCG32_SPMV,     // float32 inner solves of mixed-precision Backward Euler
+    K_PCG32_UPDATE,
+    K_PCG32_REFINE,   // their right-hand-side set-up and the float64 correction x += d
     K_NCLASS
 };
 
 inline const char* kclass_name(int k) {
     static const char* names[K_NCLASS] = {"apply", "ptl_pass", "y0_stage1", "ptl_finalize", "stage1", "stage",
-                                          "pcg_init", "pcg_spmv", "pcg_update", "setup"};
+                                          "pcg_init", "pcg_spmv", "pcg_update", "setup",
+                                          "pcg32_spmv", "pcg32_update", "pcg32_refine"};
     return names[k];
 }
 
@@ -66,6 +70,14 @@ struct Prof {
     }
     void reset() {
         for (int k = 0; k < K_NCLASS; ++k) { launches[k] = 0; ms[k] = 0.0; bytes[k] = 0.0; timed[k] = 0; }
+    }
+    // Moves the totals of class `from` of another (harvested) record into class `to` of this one.
+    void absorb(Prof& o, int from, int to) {
+        launches[to] += o.launches[from];
+        ms[to] += o.ms[from];
+        bytes[to] += o.bytes[from];
+        timed[to] += o.timed[from];
+        o.launches[from] = 0; o.ms[from] = 0.0; o.bytes[from] = 0.0; o.timed[from] = 0;
     }
     void release() {
         harvest();

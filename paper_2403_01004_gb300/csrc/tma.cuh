@@ -65,7 +65,7 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
 
 // Host: the tensor maps one TMA march launch needs (all for one scalar field grid).
 struct TmaMaps {
-    CUtensorMap halo;      // input field, box (TX + 2 HX) x (TY + 2) x 1
+    CUtensorMap halo[3];   // arrays of the input field, box (TX + 2 HX) x (TY + 2) x 1
     CUtensorMap coef;      // coefficient records, box 4 x (TX + 1) x (TY + 1) x 1
     CUtensorMap cen[3];    // point operands of the epilogue, box TX x TY x 1
 };
