@@ -13,6 +13,8 @@ neighbour difference at k towards zero, so the next dt_PTL collapses and the loo
 floor = 0 gives the literal rule.  Without the PTL the step is
 one cycle of length dt.  A forced schedule (a list of cycle lengths) replaces the PTL decision;
 it is used to compare runs whose PTL decisions are taken in different precisions.
+ptl_mode="full" takes dt_PTL from the Eq. 4 condition over every pair of neighbours (ptl_full)
+instead of the F_max localisation of Eq. 5; the cycle rule is the same.
 """
 from __future__ import annotations
 
@@ -22,7 +24,7 @@ import math
 import numpy as np
 
 from .pcg import be_solve
-from .ptl import ptl
+from .ptl import ptl, ptl_full
 from .sts import SCHEMES, TIE, sts_step
 
 
@@ -44,7 +46,7 @@ class CycleLog:
         return len(self.dt_c)
 
 
-def _cycles(op, u, dt, use_ptl, forced, max_cycles, log, needs_F_always, floor):
+def _cycles(op, u, dt, use_ptl, forced, max_cycles, log, needs_F_always, floor, ptl_mode="fmax"):
     """Generator over cycles: yields (dt_c, F(u) or None) and receives the new state."""
     t_rem = dt
     c = 0
@@ -63,7 +65,11 @@ def _cycles(op, u, dt, use_ptl, forced, max_cycles, log, needs_F_always, floor):
                 raise MaxCyclesError(f"more than {max_cycles} cycles")
             F = op.apply(u) if (use_ptl or needs_F_always) else None
             if use_ptl:
-                dtp, k, _ = ptl(op, u, F)
+                if ptl_mode == "full":
+                    dtp, key = ptl_full(op, u, F)
+                    k = key // 3 if key >= 0 else -1
+                else:
+                    dtp, k, _ = ptl(op, u, F)
                 dtl = max(dtp, floor * dtE)
                 q = t_rem / dtl * TIE
                 n = 1.0 if q <= 1.0 else math.ceil(q)
@@ -80,13 +86,13 @@ def _cycles(op, u, dt, use_ptl, forced, max_cycles, log, needs_F_always, floor):
 
 
 def sts_advance(op, u, dt: float, scheme: str = "rkl2", use_ptl: bool = True, forced=None,
-                max_cycles: int = 100000, floor: float = 1.0):
+                max_cycles: int = 100000, floor: float = 1.0, ptl_mode: str = "fmax"):
     """Advance u over dt with RKL2 / RKG2 and PTL cycling.  Returns (u_new, CycleLog)."""
     stages, coeffs = SCHEMES[scheme]
     dtE = op.dt_explicit()
     u = np.array(u, dtype=np.float64, copy=True)
     log = CycleLog()
-    gen = _cycles(op, u, dt, use_ptl, forced, max_cycles, log, True, floor)
+    gen = _cycles(op, u, dt, use_ptl, forced, max_cycles, log, True, floor, ptl_mode)
     try:
         dt_c, y0 = next(gen)
         while True:
@@ -100,11 +106,12 @@ def sts_advance(op, u, dt: float, scheme: str = "rkl2", use_ptl: bool = True, fo
 
 
 def be_advance(op, u, dt: float, use_ptl: bool = True, rtol: float = 1e-10, max_iter: int = 100000,
-               forced=None, max_cycles: int = 100000, fixed_iters: int = 0, floor: float = 1.0):
+               forced=None, max_cycles: int = 100000, fixed_iters: int = 0, floor: float = 1.0,
+               ptl_mode: str = "fmax"):
     """Advance u over dt with Backward Euler + PCG and PTL cycling."""
     u = np.array(u, dtype=np.float64, copy=True)
     log = CycleLog()
-    gen = _cycles(op, u, dt, use_ptl, forced, max_cycles, log, False, floor)
+    gen = _cycles(op, u, dt, use_ptl, forced, max_cycles, log, False, floor, ptl_mode)
     try:
         dt_c, _ = next(gen)
         while True:

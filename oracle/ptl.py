@@ -10,6 +10,12 @@ dt <= -du/dF (Eq. 4).  The condition is evaluated only at k = argmax |F| over al
 Readings fixed by the project: ties in |F| go to the smallest flat index (component first, then
 r fastest); neighbours that do not satisfy the Eq. 4 case are skipped (Eq. 5 written literally
 would admit negative ratios); with no qualifying neighbour dt_PTL = +inf.
+
+ptl_full drops the localisation: Sec. 2 notes that the Eq. 4 condition can be checked over every
+cell in every direction and the minimum taken, which Eq. 5 avoids by assuming the minimum lies at
+F_max.  Every unordered pair of face neighbours (i, j) of one component is taken once, as
+(i, i + e_d) with d = 0 (r), 1 (theta), 2 (phi, periodic); -du/dF is symmetric in i and j.  Ties in
+the bound go to the smallest key 3 i + d.
 """
 from __future__ import annotations
 
@@ -28,3 +34,34 @@ def ptl(op, u: np.ndarray, F: np.ndarray):
         if du != 0.0 and dF != 0.0 and du * dF < 0.0:
             best = min(best, -du / dF)
     return best, k, float(abs(F[k]))
+
+
+def ptl_full(op, u: np.ndarray, F: np.ndarray):
+    """Returns (dt, key): the smallest Eq. 4 bound over all pairs of face neighbours and the pair
+    (i, i + e_d) as key = 3 i + d, or (inf, -1) when no pair qualifies."""
+    offsets = getattr(op, "offsets", [0])
+    best, best_key = math.inf, -1
+    for shape, off in zip(op.shapes, offsets):
+        n = int(np.prod(shape))
+        U = u[off:off + n].reshape(shape)
+        G = F[off:off + n].reshape(shape)
+        idx = off + np.arange(n, dtype=np.int64).reshape(shape)
+        # (cell, neighbour) arrays per direction; axes are (phi, theta, r)
+        pairs = [
+            (U[:, :, :-1], U[:, :, 1:], G[:, :, :-1], G[:, :, 1:], idx[:, :, :-1], 0),
+            (U[:, :-1, :], U[:, 1:, :], G[:, :-1, :], G[:, 1:, :], idx[:, :-1, :], 1),
+            (U, np.roll(U, -1, axis=0), G, np.roll(G, -1, axis=0), idx, 2),
+        ]
+        for ua, ub, fa, fb, ia, d in pairs:
+            du = ua - ub
+            dF = fa - fb
+            ok = (du != 0.0) & (dF != 0.0) & (du * dF < 0.0)
+            if not ok.any():
+                continue
+            bound = -du[ok] / dF[ok]
+            keys = 3 * ia[ok] + d
+            m = float(bound.min())
+            kmin = int(keys[bound == m].min())
+            if m < best or (m == best and kmin < best_key):
+                best, best_key = m, kmin
+    return best, best_key

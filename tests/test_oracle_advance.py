@@ -1,5 +1,6 @@
 """Pins of the oracle's time integration: STS and BE on eigenmodes (closed-form amplification),
-the PTL (Eq. 5) on an eigenmode and on a spike, the dynamic cycle loop on an eigenmode, the
+the PTL (Eq. 5) on an eigenmode and on a spike, the unlocalised PTL (Eq. 4 over all pairs)
+against brute force and closed forms, the dynamic cycle loop on an eigenmode, the
 Fig. 1 set-up, conservation on the sphere, and dense eigen-decomposition / Cholesky truth."""
 import math
 
@@ -13,7 +14,7 @@ from oracle.advance import be_advance, sts_advance
 from oracle.dense import apply_function, dense_matrix, symmetric_eig
 from oracle.geometry import Shell
 from oracle.pcg import be_solve
-from oracle.ptl import ptl
+from oracle.ptl import ptl, ptl_full
 from oracle.sts import rkg2_stages, rkl2_stages
 from oracle.tc import TCOperator
 from oracle.visc import ViscOperator
@@ -95,10 +96,108 @@ def test_ptl_no_candidate_is_infinite_and_ties_pick_first():
     assert dtp == math.inf and k == 0 and fmax == 0.0
 
 
+def _brute_full(shapes, u, F):
+    """Eq. 4 over all face-neighbour pairs by explicit loops: for every cell (k, j, i) of every
+    component and each direction, the neighbour one cell up (phi periodic, r and theta not)."""
+    best, key, off = math.inf, -1, 0
+    for (n_p, n_t, n_r) in shapes:
+        for k in range(n_p):
+            for j in range(n_t):
+                for i in range(n_r):
+                    a = off + (k * n_t + j) * n_r + i
+                    nbrs = []
+                    if i + 1 < n_r:
+                        nbrs.append((a + 1, 0))
+                    if j + 1 < n_t:
+                        nbrs.append((a + n_r, 1))
+                    nbrs.append((off + (((k + 1) % n_p) * n_t + j) * n_r + i, 2))
+                    for b, d in nbrs:
+                        du, dF = u[a] - u[b], F[a] - F[b]
+                        if du != 0.0 and dF != 0.0 and du * dF < 0.0:
+                            r = -du / dF
+                            if r < best or (r == best and 3 * a + d < key):
+                                best, key = r, 3 * a + d
+        off += n_p * n_t * n_r
+    return best, key
+
+
+@pytest.mark.parametrize("kind", ["tc", "visc"])
+def test_ptl_full_matches_brute_force(kind):
+    """Random states and random F (every sign case), then small-integer values (many exact ties,
+    zero differences): same bound and same pair as the explicit loops."""
+    rng = np.random.default_rng(7)
+    op = tc_box((3, 4, 5), (0.6, 0.0, 0.8)) if kind == "tc" else visc_box((3, 4, 5))
+    for _ in range(3):
+        u = rng.standard_normal(op.n)
+        F = rng.standard_normal(op.n)
+        assert ptl_full(op, u, F) == _brute_full(op.shapes, u, F)
+        u = rng.integers(-2, 3, op.n).astype(float)
+        F = rng.integers(-3, 4, op.n).astype(float)
+        assert ptl_full(op, u, F) == _brute_full(op.shapes, u, F)
+
+
+def test_ptl_full_closed_forms():
+    """Eigenmode: every qualifying pair gives -1/lambda.  Point spike under the 7-point
+    Laplacian: only the six spike pairs qualify, each 1/7; the smallest key is the -phi pair."""
+    shape = (8, 6, 10)
+    b = np.array([0.36, 0.48, 0.8])
+    op = tc_box(shape, b)
+    u, th = mode(shape, (2, 1, 1))
+    lam = tc_symbol(th, b)
+    dt, key = ptl_full(op, u, op.apply(u))
+    assert dt == pytest.approx(-1.0 / lam, rel=1e-12)
+    vop = visc_box((5, 5, 9))
+    s = vop.offsets[1] + 4 + 9 * (2 + 5 * 2)
+    v = np.zeros(vop.n); v[s] = 1.0
+    dt, key = ptl_full(vop, v, vop.apply(v))
+    assert dt == pytest.approx(1.0 / 7.0, rel=1e-14)
+    assert key == 3 * (s - 45) + 2
+    assert ptl_full(vop, np.zeros(vop.n), np.zeros(vop.n)) == (math.inf, -1)
+
+
+def test_ptl_full_differs_from_fmax_localisation():
+    """Planes along r under the 3-point Laplacian (bhat along r, h = 1): a spike of height 10
+    holds max |F| = 20, where Eq. 5 gives h^2/3; a checkerboard patch of height 0.1 elsewhere
+    has |F| <= 0.4, but each pair inside it gives -du/dF = 2/8 = 1/4, the full-grid minimum."""
+    op = tc_box((3, 3, 24), (1.0, 0.0, 0.0))
+    u = np.zeros(op.shape)
+    u[:, :, 4] = 10.0
+    for i in range(12, 18):
+        u[:, :, i] = 0.1 * (-1.0) ** i
+    u = u.reshape(-1)
+    F = op.apply(u)
+    dtp, k, fmax = ptl(op, u, F)
+    assert k % 24 == 4 and fmax == pytest.approx(20.0, rel=1e-14)
+    assert dtp == pytest.approx(1.0 / 3.0, rel=1e-14)
+    dt, key = ptl_full(op, u, F)
+    assert dt == pytest.approx(0.25, rel=1e-14)
+    assert 11 <= (key // 3) % 24 <= 17 and key % 3 == 0
+    assert dt == pytest.approx(0.5 * op.dt_explicit(), rel=1e-14)
+
+
+@pytest.mark.parametrize("kind", ["tc", "visc"])
+def test_ptl_full_never_above_fmax_localisation(kind):
+    """The localised bound is a minimum over a subset of the pairs."""
+    wl = synth.make_grid(12, 10, 8, 1.05)
+    for seed in range(3):
+        if kind == "tc":
+            inp = synth.tc_inputs(wl, 100 + seed, noise=0.05)
+            op = TCOperator.spherical(Shell(wl.r_face, wl.t_face, wl.n_phi), inp.T, inp.n, inp.B)
+            u = inp.T.reshape(-1)
+        else:
+            vi = synth.visc_inputs(wl, 100 + seed)
+            op = ViscOperator.spherical(Shell(wl.r_face, wl.t_face, wl.n_phi), vi.rho, vi.nu)
+            u = np.concatenate([c.reshape(-1) for c in vi.v])
+        F = op.apply(u)
+        assert ptl_full(op, u, F)[0] <= ptl(op, u, F)[0]
+
+
+@pytest.mark.parametrize("ptl_mode", ["fmax", "full"])
 @pytest.mark.parametrize("scheme", ["rkl2", "rkg2"])
-def test_cycle_loop_on_eigenmode(scheme):
+def test_cycle_loop_on_eigenmode(scheme, ptl_mode):
     """On an eigenmode the PTL stays 1/|lambda| after every cycle (the mode only scales), so the
-    loop takes n = ceil(dt |lambda|) equal cycles and returns R_s(dt_c lambda)^n u."""
+    loop takes n = ceil(dt |lambda|) equal cycles and returns R_s(dt_c lambda)^n u; the same for
+    the unlocalised PTL, every qualifying pair giving 1/|lambda|."""
     shape = (8, 6, 10)
     b = np.array([0.36, 0.48, 0.8])
     op = tc_box(shape, b)
@@ -108,7 +207,7 @@ def test_cycle_loop_on_eigenmode(scheme):
     # ~10 cycles: over many more, rounding-level components of faster-decaying-under-R modes
     # grow relative to the mode and the PTL drifts (a property of the schemes, not of the loop)
     dt = 9.3 / abs(lam)
-    un, log = sts_advance(op, u, dt, scheme, use_ptl=True)
+    un, log = sts_advance(op, u, dt, scheme, use_ptl=True, ptl_mode=ptl_mode)
     n = math.ceil(dt * abs(lam))
     assert log.cycles == n
     dt_c = dt / n
@@ -117,7 +216,7 @@ def test_cycle_loop_on_eigenmode(scheme):
     np.testing.assert_allclose(log.dt_c, dt_c, rtol=1e-10)
     np.testing.assert_allclose(un, R_closed(scheme, s, dt_c * lam) ** n * u, atol=1e-12)
     # BE takes the same schedule and gives (1 - dt_c lambda)^-n
-    ub, logb = be_advance(op, u, dt, use_ptl=True, rtol=1e-14)
+    ub, logb = be_advance(op, u, dt, use_ptl=True, rtol=1e-14, ptl_mode=ptl_mode)
     assert logb.cycles == n
     np.testing.assert_allclose(ub, u / (1.0 - dt_c * lam) ** n, atol=1e-11)
 
