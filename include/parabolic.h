@@ -63,6 +63,9 @@ extern "C" {
 typedef enum { PB_FP64 = 0, PB_FP32 = 1, PB_BF16_STORE = 2 } pb_precision;
 typedef enum { PB_TC_ANISO = 0, PB_VISC_ISO = 1 } pb_op_kind;
 typedef enum { PB_RKL2 = 0, PB_RKG2 = 1 } pb_scheme;
+/* Where the PTL condition is evaluated: at argmax |F| only (Eq. 5) or over every pair of face
+ * neighbours (Eq. 4 without the F_max localisation; Sec. 2, the text after Eq. 4). */
+typedef enum { PB_PTL_FMAX = 0, PB_PTL_FULL = 1 } pb_ptl_mode;
 
 typedef struct pb_ctx pb_ctx;
 
@@ -106,7 +109,10 @@ typedef struct {
                                  has the smaller initial residual ||b - S x||; 0 uses x0     */
     int32_t mixed_precision;  /* BE on a PB_FP64 context: 1 solves by iterative refinement --
                                  float64 residuals, float32 PCG corrections (default 0)      */
-    double inner_rtol;        /* relative residual of each float32 correction (default 1e-3) */
+    double inner_rtol;        /* relative residual of each float32 correction (default 1e-3;
+                                 the last correction stops once the outer test is met)      */
+    int32_t ptl_mode;         /* PB_PTL_FMAX (default) or PB_PTL_FULL: the PTL value that
+                                 sets each cycle                                            */
 } pb_advance_opts;
 
 /* Statistics of an advance call (host struct).  The per-cycle arrays are optional caller-owned
@@ -124,9 +130,12 @@ typedef struct {
     int32_t cycle_capacity;
     double* dt_cycle;          /* cycle lengths                                             */
     int32_t* work_cycle;       /* STS stages s, or PCG iterations, per cycle                */
-    double* dt_ptl_cycle;      /* PTL value before each cycle (NaN when not evaluated)      */
+    double* dt_ptl_cycle;      /* PTL value that set each cycle (NaN when not evaluated)    */
     int64_t* k_cycle;          /* argmax |F| location before each cycle (-1 when not)       */
     int32_t guess_used;        /* BE: 1 if the first solve started from x0, 0 from u^n      */
+    double* dt_full_cycle;     /* Eq. 4 over every pair of face neighbours before each cycle;
+                                  when non-NULL it is evaluated every cycle whatever ptl_mode
+                                  (a second reduction pass over u and F), NaN when not      */
 } pb_stats;
 
 /* Fills *opts with the defaults listed above. */
@@ -169,6 +178,16 @@ PB_API int parabolic_apply(pb_ctx* ctx, const void* u_dev, void* F_dev);
  * max |F| (ties: smallest index) and |F_k|.  Any output pointer may be NULL. */
 PB_API int ptl_compute(pb_ctx* ctx, const void* u_dev, double* dt_ptl, int64_t* k_index,
                 double* fmax);
+
+/* PTL without the F_max localisation (Sec. 2, the text after Eq. 4): the smallest bound -du/dF
+ * of Eq. 4 over every pair of face neighbours (i, i + e_d) of state u, each component on its own,
+ * d = 0 (r), 1 (theta), 2 (phi, periodic), over the pairs with du = u_i - u_j != 0,
+ * dF = F_i - F_j != 0 and du dF < 0 (F = L u, computed here; bounds in the arithmetic
+ * precision).  Outputs: dt_full (+INF when no pair qualifies), the pair's flat cell index i and
+ * direction d (both -1 then); equal bounds go to the smallest 3 i + d.  Any output pointer may
+ * be NULL.  Returns PB_OK, PB_EINVAL, PB_ENONFINITE (non-finite F) or PB_ECUDA. */
+PB_API int ptl_full_compute(pb_ctx* ctx, const void* u_dev, double* dt_full, int64_t* cell,
+                            int32_t* direction);
 
 /* Advances u (device, in place, ctx precision) over dt with RKL2 or RKG2 super time stepping
  * (opts->scheme) under PTL cycling (Appendix A stage loop).  stats may be NULL. */

@@ -23,12 +23,14 @@ PB_RKL2, PB_RKG2 = 0, 1
 
 PRECISIONS = {"fp64": PB_FP64, "fp32": PB_FP32, "bf16": PB_BF16_STORE}
 SCHEMES = {"rkl2": PB_RKL2, "rkg2": PB_RKG2}
+PB_PTL_FMAX, PB_PTL_FULL = 0, 1
+PTL_MODES = {"fmax": PB_PTL_FMAX, "full": PB_PTL_FULL}
 C_TC = (5.0 / 3.0 - 1.0) / 2.0
 
 # C function names exported by the library (kept in step with include/parabolic.h)
 EXPORTS = ("pb_advance_opts_init", "pb_status_string", "pb_last_error", "parabolic_setup",
            "parabolic_update", "parabolic_destroy", "parabolic_state_size", "parabolic_dt_explicit", "parabolic_apply",
-           "ptl_compute", "rkl2_advance", "be_pcg_advance", "pb_profile_enable", "pb_profile_read",
+           "ptl_compute", "ptl_full_compute", "rkl2_advance", "be_pcg_advance", "pb_profile_enable", "pb_profile_read",
            "pb_ptl_noalloc", "pb_tune_init", "pb_batch_create", "pb_batch_destroy", "pb_batch_last_error",
            "pb_batch_rkl2_advance", "pb_autotune", "pb_model_create", "pb_model_destroy", "pb_model_last_error",
            "pb_model_num_params", "pb_model_get_params", "pb_model_set_params", "pb_model_save", "pb_model_load",
@@ -50,7 +52,7 @@ class PbAdvanceOpts(ctypes.Structure):
                 ("ptl_floor", c_double), ("dt_cycles", POINTER(c_double)), ("n_forced", c_int32),
                 ("rtol", c_double), ("max_iter", c_int32), ("fixed_iters", c_int32),
                 ("check_every", c_int32), ("judge_guess", c_int32), ("mixed_precision", c_int32),
-                ("inner_rtol", c_double)]
+                ("inner_rtol", c_double), ("ptl_mode", c_int32)]
 
 
 class PbStats(ctypes.Structure):
@@ -59,7 +61,8 @@ class PbStats(ctypes.Structure):
                 ("fmax", c_double), ("k_index", c_int64), ("final_rel_residual", c_double),
                 ("cycle_capacity", c_int32), ("dt_cycle", POINTER(c_double)),
                 ("work_cycle", POINTER(c_int32)), ("dt_ptl_cycle", POINTER(c_double)),
-                ("k_cycle", POINTER(c_int64)), ("guess_used", c_int32)]
+                ("k_cycle", POINTER(c_int64)), ("guess_used", c_int32),
+                ("dt_full_cycle", POINTER(c_double))]
 
 
 class PbKernelStat(ctypes.Structure):
@@ -297,8 +300,20 @@ def ptl_compute(ctx: Context, u):
     return dt.value, k.value, fm.value
 
 
+def ptl_full_compute(ctx: Context, u):
+    """Returns (dt, cell, direction): Eq. 4 over every pair of face neighbours of state u (the PTL
+    without the F_max localisation); the pair is (cell, cell + e_direction), direction 0 r,
+    1 theta, 2 phi; (inf, -1, -1) when no pair qualifies."""
+    _check_state(ctx, u)
+    dt, cell, d = c_double(), c_int64(), c_int32()
+    _check(load_library().ptl_full_compute(ctx.handle, c_void_p(_ptr(u)), byref(dt), byref(cell), byref(d)),
+           ctx.handle)
+    return dt.value, cell.value, d.value
+
+
 def _opts(scheme="rkl2", use_ptl=True, max_cycles=0, ptl_floor=1.0, forced=None, rtol=1e-10,
-          max_iter=100000, fixed_iters=0, check_every=8, judge_guess=True, mixed=False, inner_rtol=1e-3):
+          max_iter=100000, fixed_iters=0, check_every=8, judge_guess=True, mixed=False, inner_rtol=1e-3,
+          ptl_mode="fmax"):
     lib = load_library()
     o = PbAdvanceOpts()
     lib.pb_advance_opts_init(byref(o))
@@ -318,12 +333,14 @@ def _opts(scheme="rkl2", use_ptl=True, max_cycles=0, ptl_floor=1.0, forced=None,
     o.judge_guess = 1 if judge_guess else 0
     o.mixed_precision = 1 if mixed else 0
     o.inner_rtol = float(inner_rtol)
+    o.ptl_mode = PTL_MODES[ptl_mode]
     return o, keep
 
 
 class _StatsBuf:
-    def __init__(self, cap: int):
+    def __init__(self, cap: int, record_full: bool = False):
         self.cap = cap
+        self.full = (c_double * cap)() if record_full else None
         self.dt = (c_double * cap)()
         self.work = (c_int32 * cap)()
         self.dtp = (c_double * cap)()
@@ -334,6 +351,8 @@ class _StatsBuf:
         self.st.work_cycle = ctypes.cast(self.work, POINTER(c_int32))
         self.st.dt_ptl_cycle = ctypes.cast(self.dtp, POINTER(c_double))
         self.st.k_cycle = ctypes.cast(self.k, POINTER(c_int64))
+        if self.full is not None:
+            self.st.dt_full_cycle = ctypes.cast(self.full, POINTER(c_double))
 
     def as_dict(self) -> dict:
         s = self.st
@@ -342,16 +361,19 @@ class _StatsBuf:
                     dt_explicit=s.dt_explicit, last_dt_ptl=s.last_dt_ptl, fmax=s.fmax, k_index=s.k_index,
                     final_rel_residual=s.final_rel_residual, status_cycle=s.status_cycle,
                     dt_cycle=list(self.dt[:n]), work_cycle=list(self.work[:n]),
-                    dt_ptl_cycle=list(self.dtp[:n]), k_cycle=list(self.k[:n]), guess_used=s.guess_used)
+                    dt_ptl_cycle=list(self.dtp[:n]), k_cycle=list(self.k[:n]), guess_used=s.guess_used,
+                    dt_full_cycle=list(self.full[:n]) if self.full is not None else None)
 
 
 def rkl2_advance(ctx: Context, u, dt: float, scheme: str = "rkl2", use_ptl: bool = True,
                  forced=None, max_cycles: int = 0, ptl_floor: float = 1.0, stats_capacity: int = 4096,
-                 raise_on_error: bool = True) -> dict:
-    """Advances u in place over dt with RKL2 / RKG2 under PTL cycling; returns the statistics."""
+                 raise_on_error: bool = True, ptl_mode: str = "fmax", record_full: bool = False) -> dict:
+    """Advances u in place over dt with RKL2 / RKG2 under PTL cycling; returns the statistics.
+    ptl_mode "full" sets the cycles from Eq. 4 over every pair of neighbours instead of Eq. 5;
+    record_full also evaluates that value before every cycle (stats "dt_full_cycle")."""
     _check_state(ctx, u)
-    o, keep = _opts(scheme, use_ptl, max_cycles, ptl_floor, forced)
-    sb = _StatsBuf(stats_capacity)
+    o, keep = _opts(scheme, use_ptl, max_cycles, ptl_floor, forced, ptl_mode=ptl_mode)
+    sb = _StatsBuf(stats_capacity, record_full)
     rc = load_library().rkl2_advance(ctx.handle, c_void_p(_ptr(u)), float(dt), byref(o), byref(sb.st))
     d = sb.as_dict()
     d["status"] = rc
@@ -364,14 +386,14 @@ def be_pcg_advance(ctx: Context, u, dt: float, use_ptl: bool = True, forced=None
                    max_iter: int = 100000, fixed_iters: int = 0, x0=None, max_cycles: int = 0,
                    ptl_floor: float = 1.0, check_every: int = 8, stats_capacity: int = 4096,
                    raise_on_error: bool = True, judge_guess: bool = True, mixed: bool = False,
-                   inner_rtol: float = 1e-3) -> dict:
+                   inner_rtol: float = 1e-3, ptl_mode: str = "fmax", record_full: bool = False) -> dict:
     """Advances u in place over dt with Backward Euler + point-Jacobi PCG under PTL cycling.
     With x0 (first cycle's initial guess) and judge_guess, the solve starts from whichever of
     x0 and u has the smaller initial residual."""
     _check_state(ctx, u)
     o, keep = _opts("rkl2", use_ptl, max_cycles, ptl_floor, forced, rtol, max_iter, fixed_iters, check_every,
-                    judge_guess, mixed, inner_rtol)
-    sb = _StatsBuf(stats_capacity)
+                    judge_guess, mixed, inner_rtol, ptl_mode)
+    sb = _StatsBuf(stats_capacity, record_full)
     x0p = c_void_p(_ptr(x0)) if x0 is not None else c_void_p(0)
     rc = load_library().be_pcg_advance(ctx.handle, c_void_p(_ptr(u)), float(dt), byref(o), x0p, byref(sb.st))
     d = sb.as_dict()

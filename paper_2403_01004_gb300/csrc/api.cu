@@ -143,6 +143,7 @@ pb_advance_opts resolve(const pb_advance_opts* o) {
     if (r.check_every <= 0) r.check_every = 8;
     if (!(r.inner_rtol > 0.0) || !(r.inner_rtol < 1.0)) r.inner_rtol = 1e-3;
     if (r.scheme != PB_RKL2 && r.scheme != PB_RKG2) throw Error{PB_EINVAL, "unknown scheme"};
+    if (r.ptl_mode != PB_PTL_FMAX && r.ptl_mode != PB_PTL_FULL) throw Error{PB_EINVAL, "unknown ptl_mode"};
     if (r.dt_cycles == nullptr) r.n_forced = 0;
     if (r.n_forced < 0) throw Error{PB_EINVAL, "n_forced < 0"};
     return r;
@@ -162,7 +163,7 @@ void stats_begin(pb_stats* st, const Ctx& c) {
     st->guess_used = 0;
 }
 
-void stats_cycle(pb_stats* st, double dt_c, int work, double dtp, long long k) {
+void stats_cycle(pb_stats* st, double dt_c, int work, double dtp, long long k, double dt_full) {
     if (!st) return;
     const int c = st->cycles;
     if (c < st->cycle_capacity) {
@@ -170,6 +171,7 @@ void stats_cycle(pb_stats* st, double dt_c, int work, double dtp, long long k) {
         if (st->work_cycle) st->work_cycle[c] = work;
         if (st->dt_ptl_cycle) st->dt_ptl_cycle[c] = dtp;
         if (st->k_cycle) st->k_cycle[c] = k;
+        if (st->dt_full_cycle) st->dt_full_cycle[c] = dt_full;
     }
     st->cycles = c + 1;
 }
@@ -211,9 +213,11 @@ double cycle_length(double t_rem, double dt_ptl, double floor_dt) {
 }
 
 // Runs the PTL pass on u (y0 = F(u) in c.y0) and returns the result (host).
-PtlResult run_ptl(Ctx& c, Ops* ops, const void* u) {
+// PTL pass: F = L u into c.y0 with Eq. 5 at argmax |F|, and with `full` Eq. 4 over every pair.
+PtlResult run_ptl(Ctx& c, Ops* ops, const void* u, bool full = false) {
     ops->y0_pass(c, u, c.y0, true, nullptr, 0.0);
     ops->ptl_finalize(c, u, c.y0);
+    if (full) ops->ptl_full(c, u, c.y0);
     PB_CUDA_TRY(cudaMemcpyAsync(c.h_ptl, c.d_ptl, sizeof(PtlResult), cudaMemcpyDeviceToHost, c.stream));
     sync(c);
     return *c.h_ptl;
@@ -248,6 +252,7 @@ void pb_advance_opts_init(pb_advance_opts* o) {
     o->judge_guess = 1;
     o->mixed_precision = 0;
     o->inner_rtol = 1e-3;
+    o->ptl_mode = PB_PTL_FMAX;
 }
 
 const char* pb_status_string(int s) {
@@ -423,6 +428,19 @@ int ptl_compute(pb_ctx* h, const void* u, double* dt_ptl, int64_t* k, double* fm
     });
 }
 
+int ptl_full_compute(pb_ctx* h, const void* u, double* dt_full, int64_t* cell, int32_t* direction) {
+    if (!h) return PB_EINVAL;
+    Ctx& c = h->c;
+    return guarded(&c, [&] {
+        if (!u) throw Error{PB_EINVAL, "null state pointer"};
+        const PtlResult r = run_ptl(c, ops_of(c), u, true);
+        if (r.nonfinite) throw Error{PB_ENONFINITE, "non-finite F in the PTL pass"};
+        if (dt_full) *dt_full = r.dt_full;
+        if (cell) *cell = r.key_full >= 0 ? r.key_full / 3 : -1;
+        if (direction) *direction = r.key_full >= 0 ? (int32_t)(r.key_full % 3) : -1;
+    });
+}
+
 int rkl2_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, pb_stats* st) {
     if (!h) return PB_EINVAL;
     Ctx& c = h->c;
@@ -434,10 +452,11 @@ int rkl2_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, pb_
         if (!(dt >= 0.0) || std::isinf(dt)) throw Error{PB_EINVAL, "dt must be finite and >= 0"};
         Ops* ops = ops_of(c);
         const bool forced = o.n_forced > 0;
+        const bool want_full = o.ptl_mode == PB_PTL_FULL || (st && st->dt_full_cycle);
         double t_rem = dt;
         Sts co;
         for (cycle = 0;; ++cycle) {
-            double dt_c, dtp = std::numeric_limits<double>::quiet_NaN();
+            double dt_c, dtp = std::numeric_limits<double>::quiet_NaN(), dfull = dtp;
             long long kk = -1;
             bool y0_done = false;
             if (forced) {
@@ -448,11 +467,13 @@ int rkl2_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, pb_
                 if (!(t_rem > 1e-12 * dt)) break;
                 if (cycle >= o.max_cycles) throw Error{PB_EMAXCYCLES, "PTL cycle count above max_cycles"};
                 if (o.use_ptl) {
-                    const PtlResult r = run_ptl(c, ops, u);
+                    const PtlResult r = run_ptl(c, ops, u, want_full);
                     if (r.nonfinite) throw Error{PB_ENONFINITE, "non-finite F in the PTL pass"};
                     dtp = r.dt_ptl;
+                    dfull = r.dt_full;
                     kk = r.k;
-                    if (st) { st->last_dt_ptl = r.dt_ptl; st->fmax = r.fmax; st->k_index = r.k; }
+                    if (o.ptl_mode == PB_PTL_FULL) dtp = r.dt_full;
+                    if (st) { st->last_dt_ptl = dtp; st->fmax = r.fmax; st->k_index = r.k; }
                     dt_c = cycle_length(t_rem, dtp, o.ptl_floor * c.dt_e);
                     y0_done = true;
                 } else {
@@ -477,7 +498,7 @@ int rkl2_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, pb_
                            StageCoef{co.mu[k], co.nu[k], co.mut[k] * dt_c, (co.mut[k] + co.gt[k]) * dt_c});
             }
             if (st) st->total_stages += co.s;
-            stats_cycle(st, dt_c, co.s, dtp, kk);
+            stats_cycle(st, dt_c, co.s, dtp, kk, dfull);
             t_rem -= dt_c;
         }
         sync(c);
@@ -499,10 +520,11 @@ int be_pcg_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, c
         if (!ops->supports_pcg()) throw Error{PB_ENOTSUP, "BE + PCG needs PB_FP64 or PB_FP32 storage"};
         ensure_pcg_buffers(c);
         const bool forced = o.n_forced > 0;
+        const bool want_full = o.ptl_mode == PB_PTL_FULL || (st && st->dt_full_cycle);
         const size_t bytes = (size_t)c.n * c.elem;
         double t_rem = dt;
         for (cycle = 0;; ++cycle) {
-            double dt_c, dtp = std::numeric_limits<double>::quiet_NaN();
+            double dt_c, dtp = std::numeric_limits<double>::quiet_NaN(), dfull = dtp;
             long long kk = -1;
             if (forced) {
                 if (cycle >= o.n_forced) break;
@@ -512,11 +534,13 @@ int be_pcg_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, c
                 if (!(t_rem > 1e-12 * dt)) break;
                 if (cycle >= o.max_cycles) throw Error{PB_EMAXCYCLES, "PTL cycle count above max_cycles"};
                 if (o.use_ptl) {
-                    const PtlResult r = run_ptl(c, ops, u);
+                    const PtlResult r = run_ptl(c, ops, u, want_full);
                     if (r.nonfinite) throw Error{PB_ENONFINITE, "non-finite F in the PTL pass"};
                     dtp = r.dt_ptl;
+                    dfull = r.dt_full;
                     kk = r.k;
-                    if (st) { st->last_dt_ptl = r.dt_ptl; st->fmax = r.fmax; st->k_index = r.k; }
+                    if (o.ptl_mode == PB_PTL_FULL) dtp = r.dt_full;
+                    if (st) { st->last_dt_ptl = dtp; st->fmax = r.fmax; st->k_index = r.k; }
                     dt_c = cycle_length(t_rem, dtp, o.ptl_floor * c.dt_e);
                 } else {
                     dt_c = t_rem;
@@ -607,7 +631,7 @@ int be_pcg_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, c
                 if (r.done == 2) throw Error{PB_ENONFINITE, "PCG breakdown or non-finite scalar"};
                 throw Error{PB_ENOCONVERGE, "PCG reached max_iter without meeting rtol"};
             }
-            stats_cycle(st, dt_c, (int)r.iter, dtp, kk);
+            stats_cycle(st, dt_c, (int)r.iter, dtp, kk, dfull);
             t_rem -= dt_c;
         }
         sync(c);

@@ -86,11 +86,13 @@ struct MarchGrid {
 struct ArgMax { double v; long long i; };
 
 struct PtlResult {
-    double dt_ptl;
+    double dt_ptl;         // Eq. 5 at k = argmax |F|
     double fmax;
     long long k;
     int nonfinite;
     int pad;
+    double dt_full;        // Eq. 4 over every pair of face neighbours (NaN when not evaluated)
+    long long key_full;    // its pair (i, i + e_d) as 3 i + d, -1 when none qualifies
 };
 
 struct PcgScalars {

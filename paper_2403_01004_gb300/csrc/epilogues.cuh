@@ -385,6 +385,8 @@ ptl_finalize_kernel(MarchGrid g, const typename P::S* u, const typename P::S* F,
     out.k = i;
     out.dt_ptl = 1.0 / 0.0;
     out.pad = 0;
+    out.dt_full = __longlong_as_double(0x7ff8000000000000LL);
+    out.key_full = -1;
     if (i >= 0 && i != LLONG_MAX) {
         int comp = 0;
         for (int c = 1; c < g.ncomp; ++c)
@@ -414,6 +416,66 @@ ptl_finalize_kernel(MarchGrid g, const typename P::S* u, const typename P::S* F,
         out.dt_ptl = best;
     }
     *res = out;
+}
+
+// Eq. 4 over every pair of face neighbours (i, i + e_d) of one component, d = 0 (r), 1 (theta),
+// 2 (phi, periodic), without the F_max localisation of Eq. 5: a pair with du = u_i - u_j != 0,
+// dF = F_i - F_j != 0 and du dF < 0 bounds dt by -du/dF (arithmetic precision).  Each block
+// leaves the smallest bound and, among equal bounds, the smallest key 3 i + d, as an ArgMax of
+// -bound (-inf when no pair qualifies).
+template <class P>
+__global__ void __launch_bounds__(256)
+ptl_full_kernel(MarchGrid g, long long n, const typename P::S* u, const typename P::S* F, ArgMax* part) {
+    using A = typename P::A;
+    A best = A(0);
+    long long key = LLONG_MAX;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        int comp = 0;
+        for (int c = 1; c < g.ncomp; ++c)
+            if (t >= g.c[c].offset) comp = c;
+        const CompGrid& cg = g.c[comp];
+        const long long loc = t - cg.offset;
+        const long long plane = (long long)cg.nr * cg.nt;
+        const long long kk = loc / plane;
+        const long long rem = loc - kk * plane;
+        const int j = (int)(rem / cg.nr);
+        const int i = (int)(rem - (long long)j * cg.nr);
+        const A ut = cvt<A>(u[t]), ft = cvt<A>(F[t]);
+        auto pair = [&](long long q, int d) {
+            const A du = ut - cvt<A>(u[q]);
+            const A df = ft - cvt<A>(F[q]);
+            if (du != A(0) && df != A(0) && du * df < A(0)) {
+                const A b = -du / df;
+                const long long kq = 3 * t + d;
+                if (key == LLONG_MAX || b < best || (b == best && kq < key)) {
+                    best = b;
+                    key = kq;
+                }
+            }
+        };
+        if (i + 1 < cg.nr) pair(t + 1, 0);
+        if (j + 1 < cg.nt) pair(t + cg.nr, 1);
+        pair(kk + 1 < cg.np ? t + plane : cg.offset + rem, 2);
+    }
+    double v = key == LLONG_MAX ? -(1.0 / 0.0) : -(double)best;
+    block_argmax(v, key);
+    if (threadIdx.x == 0) part[blockIdx.x] = ArgMax{v, key};
+}
+
+// One block: the smallest bound over the partials of ptl_full_kernel into res->dt_full / key_full.
+static __global__ void __launch_bounds__(256)
+ptl_full_finalize_kernel(const ArgMax* part, int nparts, PtlResult* res) {
+    double v = -(1.0 / 0.0);
+    long long i = LLONG_MAX;
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+        const ArgMax m = part[b];
+        argmax_merge(v, i, m.v, m.i);
+    }
+    block_argmax(v, i);
+    if (threadIdx.x != 0) return;
+    const bool none = i == LLONG_MAX;
+    res->dt_full = none ? 1.0 / 0.0 : -v;
+    res->key_full = none ? -1 : i;
 }
 
 }  // namespace pb

@@ -18,6 +18,8 @@ public:
     virtual void y0_pass(Ctx& c, const void* u, void* y0, bool argmax, void* d1, double a) = 0;
     // Eq. 5 at argmax |F|; result in c.d_ptl
     virtual void ptl_finalize(Ctx& c, const void* u, const void* F) = 0;
+    // Eq. 4 over every pair of face neighbours of (u, F = L u) into c.d_ptl->dt_full / key_full
+    virtual void ptl_full(Ctx& c, const void* u, const void* F) = 0;
     // d1 = a y0
     virtual void stage1(Ctx& c, const void* y0, void* d1, double a) = 0;
     // stages 1 and 2 fused (EpiStage2): from y0, writes d1 (when u0 == nullptr) and d2 into out,

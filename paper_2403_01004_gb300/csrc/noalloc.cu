@@ -13,11 +13,12 @@ namespace pb {
 namespace {
 
 constexpr size_t kScratchBytes = 1u << 20;           // 1 MiB per device that loads the library
-constexpr size_t kResultOff = 0;                      // PtlResult (32 bytes)
+constexpr size_t kResultOff = 0;                      // PtlResult (48 bytes)
 constexpr size_t kFlagOff = 64;                       // non-finite flag (int)
 constexpr size_t kPartOff = 256;                      // ArgMax partials (16 bytes per block)
 constexpr int kMaxBlocks = (int)((kScratchBytes - kPartOff) / sizeof(ArgMax));
 constexpr int kMaxDevices = 64;
+static_assert(sizeof(PtlResult) <= kFlagOff - kResultOff, "the result record overlaps the flag");
 
 static __device__ __align__(256) unsigned char g_ptl_scratch[kScratchBytes];
 

@@ -122,6 +122,18 @@ public:
         PB_CUDA_TRY(cudaGetLastError());
     }
 
+    void ptl_full(Ctx& c, const void* u, const void* F) override {
+        const int blocks = reduce_blocks(c);
+        {
+            KScope ks(c.prof, c.stream, K_PTL_FULL, nb(c, 2, 0));
+            ptl_full_kernel<P><<<blocks, 256, 0, c.stream>>>(c.grid, c.n, static_cast<const S*>(u),
+                                                             static_cast<const S*>(F), static_cast<ArgMax*>(c.partials));
+            PB_CUDA_TRY(cudaGetLastError());
+        }
+        ptl_full_finalize_kernel<<<1, 256, 0, c.stream>>>(static_cast<const ArgMax*>(c.partials), blocks, c.d_ptl);
+        PB_CUDA_TRY(cudaGetLastError());
+    }
+
     void stage1(Ctx& c, const void* y0, void* d1, double a) override {
         const int blocks = reduce_blocks(c);
         KScope ks(c.prof, c.stream, K_STAGE1, nb(c, 2, 0));

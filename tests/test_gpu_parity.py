@@ -13,7 +13,7 @@ import pytest
 from gpu_common import TOL, gpu_ctx, rel_l2, rel_max, tc_problem, to_dev, to_host, visc_problem
 from oracle.advance import be_advance, sts_advance
 from oracle.pcg import be_solve
-from oracle.ptl import ptl
+from oracle.ptl import ptl, ptl_full
 
 pytestmark = pytest.mark.gpu
 
@@ -69,16 +69,127 @@ def test_ptl_fp64(kind):
     assert fmax == pytest.approx(fo, rel=1e-12)
 
 
-def _sts_compare(kind, shape, scheme, prec, use_ptl=True, forced=None, ratio=100.0):
+def _sts_compare(kind, shape, scheme, prec, use_ptl=True, forced=None, ratio=100.0, ptl_mode="fmax"):
     import paper_2403_01004_gb300 as pb
     g, inp, op, u = tc_problem(*shape) if kind == "tc" else visc_problem(*shape)
     ctx = gpu_ctx(kind, g, inp, prec)
     dt = ratio * op.dt_explicit()
     ud = to_dev(u, ctx)
     u_in = to_host(ud)
-    st = pb.rkl2_advance(ctx, ud, dt, scheme=scheme, use_ptl=use_ptl, forced=forced)
-    uo, log = sts_advance(op, u_in, dt, scheme, use_ptl=use_ptl, forced=forced)
+    st = pb.rkl2_advance(ctx, ud, dt, scheme=scheme, use_ptl=use_ptl, forced=forced, ptl_mode=ptl_mode,
+                         record_full=True)
+    uo, log = sts_advance(op, u_in, dt, scheme, use_ptl=use_ptl, forced=forced, ptl_mode=ptl_mode)
     return st, log, to_host(ud), uo, op, u_in
+
+
+def _ptl_full_interval(op, u, F, eps):
+    """Range of the full-grid PTL when every F and u entry may be off by eps times its max norm
+    (the float64 apply tolerance): a pair's bound b = -du/dF moves, to first order, by at most
+    b (2 eps |F|_inf / |dF| + 2 eps |u|_inf / |du|); the minimum then lies between the smallest
+    lower end and the smallest upper end.  Pairs as in the oracle: (i, i + e_d), phi periodic."""
+    fi, ui = np.abs(F).max(), np.abs(u).max()
+    lo, hi = math.inf, math.inf
+    for shape, off in zip(op.shapes, getattr(op, "offsets", [0])):
+        n = int(np.prod(shape))
+        U, G = u[off:off + n].reshape(shape), F[off:off + n].reshape(shape)
+        for ua, ub, ga, gb in ((U[:, :, :-1], U[:, :, 1:], G[:, :, :-1], G[:, :, 1:]),
+                               (U[:, :-1], U[:, 1:], G[:, :-1], G[:, 1:]),
+                               (U, np.roll(U, -1, 0), G, np.roll(G, -1, 0))):
+            du, dF = ua - ub, ga - gb
+            ok = (du != 0) & (dF != 0) & (du * dF < 0)
+            if ok.any():
+                b = -du[ok] / dF[ok]
+                db = b * (2 * eps * fi / np.abs(dF[ok]) + 2 * eps * ui / np.abs(du[ok]))
+                lo, hi = min(lo, float((b - db).min())), min(hi, float((b + db).min()))
+    return lo, hi
+
+
+PTL_FULL_SHAPES = {"tc": [(40, 21, 13), (32, 32, 64), (67, 9, 5), (2, 2, 3)], "visc": [(24, 20, 16), (9, 7, 5)]}
+
+
+@pytest.mark.parametrize("kind,shape", [(k, s) for k, v in PTL_FULL_SHAPES.items() for s in v])
+def test_ptl_full_fp64(kind, shape):
+    """Eq. 4 over every pair of face neighbours: the float64 bound agrees with the oracle's (F
+    differs in the last bits: different summation order) and the pair is the oracle's; never
+    above the F_max-localised value."""
+    import paper_2403_01004_gb300 as pb
+    g, inp, op, u = tc_problem(*shape, noise=0.05) if kind == "tc" else visc_problem(*shape)
+    ctx = gpu_ctx(kind, g, inp, "fp64")
+    ud = to_dev(u, ctx)
+    dt, cell, d = pb.ptl_full_compute(ctx, ud)
+    dto, keyo = ptl_full(op, u, op.apply(u))
+    assert 3 * cell + d == keyo
+    assert dt == pytest.approx(dto, rel=1e-10)
+    assert dt <= pb.ptl_compute(ctx, ud)[0]
+
+
+@pytest.mark.parametrize("kind", ["tc", "visc"])
+def test_ptl_full_fp32(kind):
+    """Float32 state and arithmetic: the bound is within 1e-3 of the oracle's on the same
+    (rounded) state, and the GPU's pair is one whose float64 bound is that close to the minimum
+    (near-equal bounds may swap under float32 rounding of F)."""
+    import paper_2403_01004_gb300 as pb
+    g, inp, op, u = tc_problem(40, 21, 13, noise=0.05) if kind == "tc" else visc_problem(24, 20, 16)
+    ctx = gpu_ctx(kind, g, inp, "fp32")
+    ud = to_dev(u, ctx)
+    ur = to_host(ud)
+    F = op.apply(ur)
+    dt, cell, d = pb.ptl_full_compute(ctx, ud)
+    dto, keyo = ptl_full(op, ur, F)
+    assert dt == pytest.approx(dto, rel=1e-3)
+    comp = int(np.searchsorted(getattr(op, "offsets", [0, op.n]), cell, side="right") - 1)
+    n_p, n_t, n_r = op.shapes[comp]
+    off = int(getattr(op, "offsets", [0])[comp])
+    loc = cell - off
+    k, rem = divmod(loc, n_t * n_r)
+    j, i = divmod(rem, n_r)
+    nb = [cell + 1, cell + n_r, off + (((k + 1) % n_p) * n_t + j) * n_r + i][d]
+    assert -(ur[cell] - ur[nb]) / (F[cell] - F[nb]) == pytest.approx(dto, rel=1e-3)
+
+
+@pytest.mark.parametrize("kind", ["tc", "visc"])
+def test_cycles_under_full_grid_ptl_fp64(kind):
+    """STS and BE cycled by the unlocalised PTL: the float64 schedule is the oracle's, with the
+    Eq. 5 value recorded beside it; the state agrees with the oracle's."""
+    import paper_2403_01004_gb300 as pb
+    shape = (32, 32, 64) if kind == "tc" else (24, 20, 16)
+    st, log, ug, uo, op, u_in = _sts_compare(kind, shape, "rkl2", "fp64", ptl_mode="full")
+    assert st["cycles"] == log.cycles
+    assert st["work_cycle"] == log.s
+    np.testing.assert_allclose(st["dt_cycle"], log.dt_c, rtol=1e-10)
+    assert st["dt_ptl_cycle"] == st["dt_full_cycle"]
+    _check_full_values(op, u_in, log.dt_c, st["dt_full_cycle"])
+    assert rel_l2(ug, uo) <= TOL["fp64"], rel_l2(ug, uo)
+    g, inp, op, u = tc_problem(*shape) if kind == "tc" else visc_problem(*shape)
+    ctx = gpu_ctx(kind, g, inp, "fp64")
+    dt = 100.0 * op.dt_explicit()
+    ud = to_dev(u, ctx)
+    stb = pb.be_pcg_advance(ctx, ud, dt, use_ptl=True, rtol=1e-10, ptl_mode="full")
+    ub, logb = be_advance(op, u, dt, use_ptl=True, rtol=1e-10, ptl_mode="full")
+    assert stb["cycles"] == logb.cycles
+    np.testing.assert_allclose(stb["dt_cycle"], logb.dt_c, rtol=1e-9)
+
+
+@pytest.mark.parametrize("kind", ["tc", "visc"])
+def test_full_grid_ptl_recorded_beside_fmax_fp64(kind):
+    """record_full under the default mode: the cycles are the Eq. 5 schedule, and each recorded
+    full-grid value is the oracle's ptl_full of the oracle's state before that cycle."""
+    shape = (32, 32, 64) if kind == "tc" else (24, 20, 16)
+    st, log, ug, uo, op, u_in = _sts_compare(kind, shape, "rkl2", "fp64")
+    assert st["cycles"] == log.cycles
+    _check_full_values(op, u_in, log.dt_c, st["dt_full_cycle"])
+    assert all(f <= p * (1 + 1e-12) for f, p in zip(st["dt_full_cycle"], st["dt_ptl_cycle"]))
+
+
+def _check_full_values(op, u0, dt_cycles, got):
+    """Each recorded full-grid value lies in the rounding interval of the oracle's state before
+    that cycle (float64 apply tolerance, 1e-12 of the max norm)."""
+    cur = np.array(u0, dtype=np.float64)
+    for c, dt_c in enumerate(dt_cycles):
+        F = op.apply(cur)
+        lo, hi = _ptl_full_interval(op, cur, F, TOL["fp64"])
+        assert lo <= got[c] <= hi, (c, lo, got[c], hi, ptl_full(op, cur, F)[0])
+        cur, _ = sts_advance(op, cur, dt_c, "rkl2", forced=[dt_c])
 
 
 @pytest.mark.parametrize("scheme", ["rkl2", "rkg2"])
