@@ -14,8 +14,8 @@ would admit negative ratios); with no qualifying neighbour dt_PTL = +inf.
 ptl_full drops the localisation: Sec. 2 notes that the Eq. 4 condition can be checked over every
 cell in every direction and the minimum taken, which Eq. 5 avoids by assuming the minimum lies at
 F_max.  Every unordered pair of face neighbours (i, j) of one component is taken once, as
-(i, i + e_d) with d = 0 (r), 1 (theta), 2 (phi, periodic); -du/dF is symmetric in i and j.  Ties in
-the bound go to the smallest key 3 i + d.
+(i, i + e_d) with d = 0 (r), 1 (theta), 2 (phi, periodic; on the periodic box r and theta wrap
+too); -du/dF is symmetric in i and j.  Ties in the bound go to the smallest key 3 i + d.
 """
 from __future__ import annotations
 
@@ -47,11 +47,15 @@ def ptl_full(op, u: np.ndarray, F: np.ndarray):
         G = F[off:off + n].reshape(shape)
         idx = off + np.arange(n, dtype=np.int64).reshape(shape)
         # (cell, neighbour) arrays per direction; axes are (phi, theta, r)
-        pairs = [
-            (U[:, :, :-1], U[:, :, 1:], G[:, :, :-1], G[:, :, 1:], idx[:, :, :-1], 0),
-            (U[:, :-1, :], U[:, 1:, :], G[:, :-1, :], G[:, 1:, :], idx[:, :-1, :], 1),
-            (U, np.roll(U, -1, axis=0), G, np.roll(G, -1, axis=0), idx, 2),
-        ]
+        if getattr(op, "periodic", False):     # the box: r and theta wrap too
+            pairs = [(U, np.roll(U, -1, axis=a), G, np.roll(G, -1, axis=a), idx, d)
+                     for d, a in ((0, 2), (1, 1), (2, 0))]
+        else:
+            pairs = [
+                (U[:, :, :-1], U[:, :, 1:], G[:, :, :-1], G[:, :, 1:], idx[:, :, :-1], 0),
+                (U[:, :-1, :], U[:, 1:, :], G[:, :-1, :], G[:, 1:, :], idx[:, :-1, :], 1),
+                (U, np.roll(U, -1, axis=0), G, np.roll(G, -1, axis=0), idx, 2),
+            ]
         for ua, ub, fa, fb, ia, d in pairs:
             du = ua - ub
             dF = fa - fb

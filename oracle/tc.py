@@ -19,6 +19,10 @@ A = -grad^2 E, i.e.
 where p in {0,1}^3 is the cell's position inside corner c and sigma(p) = 2p - 1.  Then
 F = w A u with the cell weight w = C / (n V).  Corners on r_min, r_max and the poles are absent
 (ahat = 0), which makes every boundary zero-flux and keeps M A symmetric (M = diag(1/w)).
+
+The periodic box (TCOperator.box) is the same scheme on unit cells (h = 1, W = V = 1) with every
+corner present and all three directions periodic: the geometry on which Fourier modes are
+eigenvectors with the closed-form eigenvalues used to pin the schemes.
 """
 from __future__ import annotations
 
@@ -40,13 +44,29 @@ class TCOperator:
 
     ncomp = 1
 
-    def __init__(self, ahat: np.ndarray, w: np.ndarray):
+    def __init__(self, ahat: np.ndarray, w: np.ndarray, periodic: bool = False):
+        """periodic: r and theta wrap as phi does (the box); the PTL then has six neighbours
+        everywhere."""
         self.ahat = np.asarray(ahat, dtype=np.float64)      # (3, n_p, n_t, n_r)
         self.w3 = np.asarray(w, dtype=np.float64)            # (n_p, n_t, n_r)
         self.shape = self.w3.shape
         self.shapes = [self.shape]
         self.n = self.w3.size
         self.w = self.w3.reshape(-1)
+        self.periodic = periodic
+
+    @classmethod
+    def box(cls, T0: np.ndarray, n: np.ndarray, B, C: float = C_TC):
+        """Periodic box of unit cells: kappa_c the mean of the 8 cells' T0^{5/2} (wrapping),
+        b = B/|B| at the corners (corner [k, j, i] between cells i..i+1, j..j+1, k..k+1),
+        ahat = sqrt(kappa_c) b / 4 and w = C / n."""
+        kappa = np.asarray(T0, dtype=np.float64) ** 2.5
+        kc = sum(shift(kappa, *p) for p in CUBE) / 8.0
+        br, bt, bp = (np.asarray(b, dtype=np.float64) for b in B)
+        bmag = np.sqrt(br * br + bt * bt + bp * bp)
+        root = np.sqrt(kc)
+        ahat = np.stack([root * br / bmag, root * bt / bmag, root * bp / bmag]) / 4.0
+        return cls(ahat, C / np.asarray(n, dtype=np.float64), periodic=True)
 
     @classmethod
     def spherical(cls, shell: Shell, T0: np.ndarray, n: np.ndarray, B, C: float = C_TC):
@@ -118,25 +138,26 @@ class TCOperator:
         return 2.0 / float(np.max(self.gershgorin()))
 
     def neighbors(self, idx: int):
-        return grid_neighbors(self.shape, idx, 0)
+        return grid_neighbors(self.shape, idx, 0, self.periodic)
 
 
-def grid_neighbors(shape, idx: int, offset: int):
+def grid_neighbors(shape, idx: int, offset: int, periodic: bool = False):
     """The up-to-6 orthogonal neighbours of flat index idx (relative to `offset`) on a grid of
-    `shape` = (n_p, n_t, n_r): phi wraps, r and theta do not."""
+    `shape` = (n_p, n_t, n_r): phi wraps; r and theta wrap only on the periodic box."""
     n_p, n_t, n_r = shape
     loc = idx - offset
     k, rem = divmod(loc, n_t * n_r)
     j, i = divmod(rem, n_r)
+    at = lambda kk, jj, ii: offset + (ii % n_r) + n_r * ((jj % n_t) + n_t * (kk % n_p))
     out = []
-    if i > 0:
-        out.append(offset + loc - 1)
-    if i < n_r - 1:
-        out.append(offset + loc + 1)
-    if j > 0:
-        out.append(offset + loc - n_r)
-    if j < n_t - 1:
-        out.append(offset + loc + n_r)
-    out.append(offset + (i + n_r * (j + n_t * ((k - 1) % n_p))))
-    out.append(offset + (i + n_r * (j + n_t * ((k + 1) % n_p))))
+    if i > 0 or periodic:
+        out.append(at(k, j, i - 1))
+    if i < n_r - 1 or periodic:
+        out.append(at(k, j, i + 1))
+    if j > 0 or periodic:
+        out.append(at(k, j - 1, i))
+    if j < n_t - 1 or periodic:
+        out.append(at(k, j + 1, i))
+    out.append(at(k - 1, j, i))
+    out.append(at(k + 1, j, i))
     return out

@@ -43,9 +43,11 @@ def staggered_axes(shell: Shell, comp: int):
 class ViscOperator:
     ncomp = 3
 
-    def __init__(self, c_list, w_list):
+    def __init__(self, c_list, w_list, periodic: bool = False):
         """c_list[comp] = (c_r, c_t, c_p): coefficient of the face between a point and its +1
-        neighbour along each axis (zero on the last r / theta point); w_list[comp] = 1/(rho V)."""
+        neighbour along each axis (zero on the last r / theta point unless periodic);
+        w_list[comp] = 1/(rho V).  periodic: r and theta wrap as phi does (the box)."""
+        self.periodic = periodic
         self.c = [tuple(np.asarray(a, dtype=np.float64) for a in c) for c in c_list]
         self.w_list = [np.asarray(w, dtype=np.float64) for w in w_list]
         self.shapes = [w.shape for w in self.w_list]
@@ -89,6 +91,21 @@ class ViscOperator:
             w_list.append(1.0 / (rho * V))
         return cls(c_list, w_list)
 
+    @classmethod
+    def box(cls, rho_list, nu_list):
+        """Periodic box of unit cells: every component on the full (n_p, n_t, n_r) grid,
+        c_f = nu_f rho_f (face means, wrapping; A_f = d_f = 1) and w = 1/rho."""
+        c_list, w_list = [], []
+        for comp in range(3):
+            rho = np.asarray(rho_list[comp], dtype=np.float64)
+            nu = np.asarray(nu_list[comp], dtype=np.float64)
+            c = []
+            for ax in range(3):
+                c.append(0.5 * (nu + shift(nu, *AXES[ax])) * (0.5 * (rho + shift(rho, *AXES[ax]))))
+            c_list.append(tuple(c))
+            w_list.append(1.0 / rho)
+        return cls(c_list, w_list, periodic=True)
+
     def split(self, u):
         u = np.asarray(u, dtype=np.float64)
         return [u[self.offsets[c]:self.offsets[c + 1]].reshape(self.shapes[c]) for c in range(3)]
@@ -130,4 +147,4 @@ class ViscOperator:
 
     def neighbors(self, idx: int):
         comp = int(np.searchsorted(self.offsets, idx, side="right") - 1)
-        return grid_neighbors(self.shapes[comp], idx, int(self.offsets[comp]))
+        return grid_neighbors(self.shapes[comp], idx, int(self.offsets[comp]), self.periodic)

@@ -14,12 +14,12 @@ def tc_box(shape, bhat, kappa=1.0):
     ahat = np.empty((3,) + tuple(shape))
     for x in range(3):
         ahat[x] = np.sqrt(kappa) * bhat[x] / 4.0
-    return TCOperator(ahat, np.ones(shape))
+    return TCOperator(ahat, np.ones(shape), periodic=True)
 
 
 def visc_box(shape):
     ones = np.ones(shape)
-    return ViscOperator([(ones, ones, ones)] * 3, [ones] * 3)
+    return ViscOperator([(ones, ones, ones)] * 3, [ones] * 3, periodic=True)
 
 
 def mode(shape, m, phase=0.3):

@@ -96,9 +96,10 @@ def test_ptl_no_candidate_is_infinite_and_ties_pick_first():
     assert dtp == math.inf and k == 0 and fmax == 0.0
 
 
-def _brute_full(shapes, u, F):
+def _brute_full(shapes, u, F, periodic=False):
     """Eq. 4 over all face-neighbour pairs by explicit loops: for every cell (k, j, i) of every
-    component and each direction, the neighbour one cell up (phi periodic, r and theta not)."""
+    component and each direction, the neighbour one cell up (phi periodic; r and theta periodic
+    only on the box)."""
     best, key, off = math.inf, -1, 0
     for (n_p, n_t, n_r) in shapes:
         for k in range(n_p):
@@ -108,8 +109,12 @@ def _brute_full(shapes, u, F):
                     nbrs = []
                     if i + 1 < n_r:
                         nbrs.append((a + 1, 0))
+                    elif periodic:
+                        nbrs.append((off + (k * n_t + j) * n_r, 0))
                     if j + 1 < n_t:
                         nbrs.append((a + n_r, 1))
+                    elif periodic:
+                        nbrs.append((off + k * n_t * n_r + i, 1))
                     nbrs.append((off + (((k + 1) % n_p) * n_t + j) * n_r + i, 2))
                     for b, d in nbrs:
                         du, dF = u[a] - u[b], F[a] - F[b]
@@ -126,14 +131,49 @@ def test_ptl_full_matches_brute_force(kind):
     """Random states and random F (every sign case), then small-integer values (many exact ties,
     zero differences): same bound and same pair as the explicit loops."""
     rng = np.random.default_rng(7)
-    op = tc_box((3, 4, 5), (0.6, 0.0, 0.8)) if kind == "tc" else visc_box((3, 4, 5))
-    for _ in range(3):
-        u = rng.standard_normal(op.n)
-        F = rng.standard_normal(op.n)
-        assert ptl_full(op, u, F) == _brute_full(op.shapes, u, F)
-        u = rng.integers(-2, 3, op.n).astype(float)
-        F = rng.integers(-3, 4, op.n).astype(float)
-        assert ptl_full(op, u, F) == _brute_full(op.shapes, u, F)
+    box = tc_box((3, 4, 5), (0.6, 0.0, 0.8)) if kind == "tc" else visc_box((3, 4, 5))
+    wl = synth.make_grid(5, 4, 3, 1.05)
+    if kind == "tc":
+        inp = synth.tc_inputs(wl, 5)
+        sph = TCOperator.spherical(Shell(wl.r_face, wl.t_face, wl.n_phi), inp.T, inp.n, inp.B)
+    else:
+        vi = synth.visc_inputs(wl, 5)
+        sph = ViscOperator.spherical(Shell(wl.r_face, wl.t_face, wl.n_phi), vi.rho, vi.nu)
+    for op in (box, sph):
+        for _ in range(3):
+            u = rng.standard_normal(op.n)
+            F = rng.standard_normal(op.n)
+            assert ptl_full(op, u, F) == _brute_full(op.shapes, u, F, op.periodic)
+            u = rng.integers(-2, 3, op.n).astype(float)
+            F = rng.integers(-3, 4, op.n).astype(float)
+            assert ptl_full(op, u, F) == _brute_full(op.shapes, u, F, op.periodic)
+
+
+def test_box_builders_reduce_to_the_closed_form_symbols():
+    """Constant inputs on the periodic box: conduction F = (C/n) kappa (bhat . D)^2-symbol times u,
+    kappa = T0^{5/2}; viscosity F = (1/rho) nu rho (7-point symbol) u."""
+    shape = (6, 5, 8)
+    T0, n, C = 1.3, 0.7, 1.0 / 3.0
+    b = np.array([0.36, 0.48, 0.8])
+    op = TCOperator.box(np.full(shape, T0), np.full(shape, n), [np.full(shape, 2.5 * x) for x in b], C)
+    u, th = mode(shape, (1, 2, 3))
+    lam = (C / n) * tc_symbol(th, b, kappa=T0 ** 2.5)
+    np.testing.assert_allclose(op.apply(u), lam * u, atol=1e-12 * abs(lam))
+    vop = ViscOperator.box([np.full(shape, 0.8)] * 3, [np.full(shape, 0.05)] * 3)
+    v = np.concatenate([u, 2 * u, -u])
+    np.testing.assert_allclose(vop.apply(v), 0.05 * visc_symbol(th) * v, atol=1e-13)
+
+
+def test_box_ptl_has_six_neighbours_everywhere():
+    """A point spike at the box's corner cell (0, 0, 0): the wrapped neighbours qualify like any
+    others, 1/7 under the 7-point Laplacian, for Eq. 5 and for every pair."""
+    vop = visc_box((5, 5, 9))
+    v = np.zeros(vop.n); v[0] = 1.0
+    F = vop.apply(v)
+    assert len(set(vop.neighbors(0))) == 6
+    assert ptl(vop, v, F)[0] == pytest.approx(1.0 / 7.0, rel=1e-14)
+    dt, key = ptl_full(vop, v, F)
+    assert dt == pytest.approx(1.0 / 7.0, rel=1e-14) and key == 0
 
 
 def test_ptl_full_closed_forms():
