@@ -25,7 +25,8 @@
  * flat index i + n_r * (j + n_theta * k).  A conduction state is one such array (cells).
  * A viscosity state is the three components back to back: v_r on (n_r-1) x n_theta x n_phi
  * interior r faces, v_theta on n_r x (n_theta-1) x n_phi interior theta faces, v_phi on
- * n_r x n_theta x n_phi phi faces.  parabolic_state_size() returns the total length.
+ * n_r x n_theta x n_phi phi faces (on the periodic box all three are n_r x n_theta x n_phi).
+ * parabolic_state_size() returns the total length.
  *
  * Conventions: all device pointers are CUDA device memory of the current device; all work is
  * enqueued on the stream given to parabolic_setup; every call returns after its work is done
@@ -69,19 +70,29 @@ typedef enum { PB_PTL_FMAX = 0, PB_PTL_FULL = 1 } pb_ptl_mode;
 
 typedef struct pb_ctx pb_ctx;
 
-/* Grid: faces of the spherical shell; phi is uniform with n_phi cells over 2 pi.
- * Requires n_r >= 2, n_theta >= 2, n_phi >= 3, 0 < r_face increasing,
- * 0 <= t_face <= pi increasing.  Both arrays are host memory, read during setup only. */
+/* Geometry of a grid.  PB_SPHERICAL: the (r, theta, phi) shell of the method (Sec. 2).
+ * PB_CARTESIAN_PERIODIC: a box of unit cells (metric factors, corner and cell volumes 1), periodic
+ * in all three directions, on which Fourier modes are eigenvectors of both operators -- the
+ * closed-form checks of the schemes and the Fig. 1 set-up. */
+typedef enum { PB_SPHERICAL = 0, PB_CARTESIAN_PERIODIC = 1 } pb_geometry;
+
+/* Grid.  PB_SPHERICAL: faces of the shell, phi uniform with n_phi cells over 2 pi; requires
+ * n_r >= 2, n_theta >= 2, n_phi >= 3, 0 < r_face increasing, 0 <= t_face <= pi increasing (host
+ * arrays, read during setup only).  PB_CARTESIAN_PERIODIC: n_r, n_theta, n_phi >= 3 unit cells
+ * along the three axes; r_face and t_face are not read (may be NULL).  Zero-initialise the struct:
+ * geometry 0 is the shell. */
 typedef struct {
     int32_t n_r, n_theta, n_phi;
     const double* r_face;   /* n_r + 1 */
     const double* t_face;   /* n_theta + 1 */
+    int32_t geometry;       /* pb_geometry */
 } pb_grid;
 
 /* Operator inputs (device memory, float64, read during setup only; may be freed afterwards).
  * PB_TC_ANISO: T0 and n at cells; B (B_r, B_theta, B_phi) at corners, corner [i,j,k] being the
  *   vertex (r_face[i+1], t_face[j+1], (k+1) dphi); corners with i = n_r-1 or j = n_theta-1 are
- *   not used.  C multiplies the divergence (1/3 for gamma = 5/3).
+ *   not used on the shell (on the periodic box every corner [i,j,k], the vertex between cells
+ *   i..i+1, j..j+1, k..k+1 with wrap, is used).  C multiplies the divergence (1/3 for gamma = 5/3).
  * PB_VISC_ISO: rho[c] and nu[c] at the points of velocity component c (layout above). */
 typedef struct {
     int32_t kind;            /* pb_op_kind */

@@ -24,6 +24,7 @@ PB_RKL2, PB_RKG2 = 0, 1
 PRECISIONS = {"fp64": PB_FP64, "fp32": PB_FP32, "bf16": PB_BF16_STORE}
 SCHEMES = {"rkl2": PB_RKL2, "rkg2": PB_RKG2}
 PB_PTL_FMAX, PB_PTL_FULL = 0, 1
+PB_SPHERICAL, PB_CARTESIAN_PERIODIC = 0, 1
 PTL_MODES = {"fmax": PB_PTL_FMAX, "full": PB_PTL_FULL}
 C_TC = (5.0 / 3.0 - 1.0) / 2.0
 
@@ -39,7 +40,7 @@ EXPORTS = ("pb_advance_opts_init", "pb_status_string", "pb_last_error", "parabol
 
 class PbGrid(ctypes.Structure):
     _fields_ = [("n_r", c_int32), ("n_theta", c_int32), ("n_phi", c_int32),
-                ("r_face", POINTER(c_double)), ("t_face", POINTER(c_double))]
+                ("r_face", POINTER(c_double)), ("t_face", POINTER(c_double)), ("geometry", c_int32)]
 
 
 class PbOperator(ctypes.Structure):
@@ -218,14 +219,27 @@ class Context:
 
 def parabolic_setup(r_face, t_face, n_phi: int, kind: str, fields: dict, precision: str = "fp64",
                     C: float = C_TC, stream=None) -> Context:
-    """Builds a context.  kind = "tc" with fields T0, n, B (3 tensors at corners), or kind = "visc"
-    with fields rho, nu (lists of 3 tensors); fields are float64 CUDA tensors."""
-    lib = load_library()
-    torch = _torch()
+    """Builds a context on the spherical shell.  kind = "tc" with fields T0, n, B (3 tensors at
+    corners), or kind = "visc" with fields rho, nu (lists of 3 tensors); fields are float64 CUDA
+    tensors."""
     rf = (c_double * len(r_face))(*[float(x) for x in r_face])
     tf = (c_double * len(t_face))(*[float(x) for x in t_face])
     g = PbGrid(len(r_face) - 1, len(t_face) - 1, int(n_phi), ctypes.cast(rf, POINTER(c_double)),
-               ctypes.cast(tf, POINTER(c_double)))
+               ctypes.cast(tf, POINTER(c_double)), PB_SPHERICAL)
+    return _setup(g, kind, fields, precision, C, stream)
+
+
+def parabolic_setup_box(n_r: int, n_theta: int, n_phi: int, kind: str, fields: dict, precision: str = "fp64",
+                        C: float = C_TC, stream=None) -> Context:
+    """Builds a context on the periodic box of unit cells (PB_CARTESIAN_PERIODIC); fields as for
+    the shell, every viscosity component on the full n_r x n_theta x n_phi grid."""
+    g = PbGrid(int(n_r), int(n_theta), int(n_phi), None, None, PB_CARTESIAN_PERIODIC)
+    return _setup(g, kind, fields, precision, C, stream)
+
+
+def _setup(g, kind, fields, precision, C, stream) -> Context:
+    lib = load_library()
+    torch = _torch()
     op, keep = _operator(kind, fields, C)
     h = c_void_p()
     st = stream if stream is not None else torch.cuda.current_stream()

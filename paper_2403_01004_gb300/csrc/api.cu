@@ -41,9 +41,12 @@ void* dmalloc(size_t bytes) {
 void build_grid(Ctx& c) {
     MarchGrid& g = c.grid;
     g.ncomp = c.kind == PB_TC_ANISO ? 1 : 3;
+    const bool box = c.geometry == PB_CARTESIAN_PERIODIC;
     int dims[3][3];
-    if (c.kind == PB_TC_ANISO) {
-        dims[0][0] = c.nr; dims[0][1] = c.nt; dims[0][2] = c.np;
+    if (c.kind == PB_TC_ANISO || box) {
+        for (int a = 0; a < g.ncomp; ++a) {
+            dims[a][0] = c.nr; dims[a][1] = c.nt; dims[a][2] = c.np;
+        }
     } else {
         dims[0][0] = c.nr - 1; dims[0][1] = c.nt; dims[0][2] = c.np;
         dims[1][0] = c.nr; dims[1][1] = c.nt - 1; dims[1][2] = c.np;
@@ -69,6 +72,7 @@ void build_grid(Ctx& c) {
         cg.nchunk = nchunk;
         cg.offset = off;
         cg.block_begin = blocks;
+        cg.periodic = box ? 1 : 0;
         off += (int64_t)cg.nr * cg.nt * cg.np;
         blocks += cg.tiles_r * cg.tiles_t * nchunk;
     }
@@ -278,14 +282,19 @@ int parabolic_setup(const pb_grid* g, const pb_operator* op, int32_t precision, 
     return guarded(nullptr, [&] {
         if (!g || !op || !out) throw Error{PB_EINVAL, "null argument"};
         *out = nullptr;
-        if (g->n_r < 2 || g->n_theta < 2 || g->n_phi < 3) throw Error{PB_EINVAL, "need n_r >= 2, n_theta >= 2, n_phi >= 3"};
-        if (!g->r_face || !g->t_face) throw Error{PB_EINVAL, "null face array"};
-        if (!(g->r_face[0] > 0.0)) throw Error{PB_EINVAL, "r_face[0] must be > 0"};
-        for (int i = 0; i < g->n_r; ++i)
-            if (!(g->r_face[i + 1] > g->r_face[i])) throw Error{PB_EINVAL, "r_face must increase"};
-        if (!(g->t_face[0] >= 0.0) || !(g->t_face[g->n_theta] <= M_PI + 1e-12)) throw Error{PB_EINVAL, "t_face outside [0, pi]"};
-        for (int j = 0; j < g->n_theta; ++j)
-            if (!(g->t_face[j + 1] > g->t_face[j])) throw Error{PB_EINVAL, "t_face must increase"};
+        if (g->geometry != PB_SPHERICAL && g->geometry != PB_CARTESIAN_PERIODIC) throw Error{PB_EINVAL, "unknown geometry"};
+        if (g->geometry == PB_CARTESIAN_PERIODIC) {
+            if (g->n_r < 3 || g->n_theta < 3 || g->n_phi < 3) throw Error{PB_EINVAL, "periodic box needs n_r, n_theta, n_phi >= 3"};
+        } else {
+            if (g->n_r < 2 || g->n_theta < 2 || g->n_phi < 3) throw Error{PB_EINVAL, "need n_r >= 2, n_theta >= 2, n_phi >= 3"};
+            if (!g->r_face || !g->t_face) throw Error{PB_EINVAL, "null face array"};
+            if (!(g->r_face[0] > 0.0)) throw Error{PB_EINVAL, "r_face[0] must be > 0"};
+            for (int i = 0; i < g->n_r; ++i)
+                if (!(g->r_face[i + 1] > g->r_face[i])) throw Error{PB_EINVAL, "r_face must increase"};
+            if (!(g->t_face[0] >= 0.0) || !(g->t_face[g->n_theta] <= M_PI + 1e-12)) throw Error{PB_EINVAL, "t_face outside [0, pi]"};
+            for (int j = 0; j < g->n_theta; ++j)
+                if (!(g->t_face[j + 1] > g->t_face[j])) throw Error{PB_EINVAL, "t_face must increase"};
+        }
         if ((long long)g->n_r * g->n_theta * g->n_phi > (1LL << 40)) throw Error{PB_EINVAL, "grid too large"};
         if (precision != PB_FP64 && precision != PB_FP32 && precision != PB_BF16_STORE) throw Error{PB_EINVAL, "bad precision"};
         if (op->kind != PB_TC_ANISO && op->kind != PB_VISC_ISO) throw Error{PB_EINVAL, "unknown operator kind"};
@@ -300,6 +309,7 @@ int parabolic_setup(const pb_grid* g, const pb_operator* op, int32_t precision, 
             c.elem = precision == PB_FP64 ? 8 : precision == PB_FP32 ? 4 : 2;
             c.stream = static_cast<cudaStream_t>(stream);
             c.nr = g->n_r; c.nt = g->n_theta; c.np = g->n_phi;
+            c.geometry = g->geometry;
             PB_CUDA_TRY(cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, dev));
             build_grid(c);
             const size_t csz = precision == PB_FP64 ? 8 : 4;
@@ -321,8 +331,9 @@ int parabolic_setup(const pb_grid* g, const pb_operator* op, int32_t precision, 
             *c.h_err = 0;
             PB_CUDA_TRY(cudaMemsetAsync(c.d_err, 0, sizeof(int), c.stream));
             {
+                // the TMA kernel fills out-of-range halo points with zeros, so only the shell uses it
                 const char* e = getenv("PB_DISABLE_TMA");
-                c.use_tma = !(e && e[0] == '1');
+                c.use_tma = !(e && e[0] == '1') && c.geometry == PB_SPHERICAL;
             }
             PB_CUDA_TRY(cudaMallocHost(&c.h_ptl, sizeof(PtlResult)));
             PB_CUDA_TRY(cudaMallocHost(&c.h_pcg, sizeof(PcgScalars)));

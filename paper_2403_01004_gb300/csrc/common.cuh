@@ -74,6 +74,7 @@ struct CompGrid {          // one scalar field (a conduction state or one veloci
     int tiles_r, tiles_t, kchunk, nchunk;
     int64_t offset;        // element offset of this component in the state / coefficient arrays
     int block_begin;       // first block index of this component in a march launch
+    int periodic;          // r and theta wrap as phi does (the periodic box)
 };
 
 struct MarchGrid {
@@ -109,6 +110,7 @@ struct Ctx {
     int elem = 8;
     cudaStream_t stream = nullptr;
     int nr = 0, nt = 0, np = 0;
+    int geometry = 0;              // pb_geometry
     MarchGrid grid{};
     int64_t n = 0;                 // state length
     double dt_e = 0.0;

@@ -400,10 +400,15 @@ ptl_finalize_kernel(MarchGrid g, const typename P::S* u, const typename P::S* F,
         const int ii = (int)(rem - (long long)jj * cg.nr);
         long long nb[6];
         int nn = 0;
+        const bool per = cg.periodic != 0;        // the box: r and theta neighbours wrap
         if (ii > 0) nb[nn++] = i - 1;
+        else if (per) nb[nn++] = i + cg.nr - 1;
         if (ii < cg.nr - 1) nb[nn++] = i + 1;
+        else if (per) nb[nn++] = i - (cg.nr - 1);
         if (jj > 0) nb[nn++] = i - cg.nr;
+        else if (per) nb[nn++] = i + (long long)(cg.nt - 1) * cg.nr;
         if (jj < cg.nt - 1) nb[nn++] = i + cg.nr;
+        else if (per) nb[nn++] = i - (long long)(cg.nt - 1) * cg.nr;
         nb[nn++] = cg.offset + (long long)((kk + cg.np - 1) % cg.np) * plane + rem;
         nb[nn++] = cg.offset + (long long)((kk + 1) % cg.np) * plane + rem;
         const double uk = (double)cvt<A>(u[i]), fk = (double)cvt<A>(F[i]);
@@ -419,7 +424,7 @@ ptl_finalize_kernel(MarchGrid g, const typename P::S* u, const typename P::S* F,
 }
 
 // Eq. 4 over every pair of face neighbours (i, i + e_d) of one component, d = 0 (r), 1 (theta),
-// 2 (phi, periodic), without the F_max localisation of Eq. 5: a pair with du = u_i - u_j != 0,
+// 2 (phi, periodic; r and theta wrap too on the periodic box), without the F_max localisation of Eq. 5: a pair with du = u_i - u_j != 0,
 // dF = F_i - F_j != 0 and du dF < 0 bounds dt by -du/dF (arithmetic precision).  Each block
 // leaves the smallest bound and, among equal bounds, the smallest key 3 i + d, as an ArgMax of
 // -bound (-inf when no pair qualifies).
@@ -454,7 +459,9 @@ ptl_full_kernel(MarchGrid g, long long n, const typename P::S* u, const typename
             }
         };
         if (i + 1 < cg.nr) pair(t + 1, 0);
+        else if (cg.periodic) pair(t - (cg.nr - 1), 0);
         if (j + 1 < cg.nt) pair(t + cg.nr, 1);
+        else if (cg.periodic) pair(t - (long long)(cg.nt - 1) * cg.nr, 1);
         pair(kk + 1 < cg.np ? t + plane : cg.offset + rem, 2);
     }
     double v = key == LLONG_MAX ? -(1.0 / 0.0) : -(double)best;

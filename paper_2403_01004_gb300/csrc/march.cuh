@@ -69,7 +69,7 @@ struct TileSmem {
     Quad<typename P::A> corn[2][TYv + 1][TXv + 1];
 };
 
-template <class P, int TXv, int TYv, class Load, class Epi>
+template <class P, int TXv, int TYv, class Load, class Epi, bool PER = false>
 __device__ __forceinline__ void tc_tile(const CompGrid& cg, const TileIdx& t, const Coef4<typename P::C>* __restrict__ coef,
                                         const Load& ld, Epi& ep, int tid, TileSmem<P, TXv, TYv>& sm) {
     using A = typename P::A;
@@ -98,13 +98,23 @@ __device__ __forceinline__ void tc_tile(const CompGrid& cg, const TileIdx& t, co
     if (tid < TYv + 1) { xci = 0; xcj = tid; }
     else if (tid < TYv + 1 + TXv) { xci = tid - TYv; xcj = 0; }
 
+    // points outside the r / theta range: zero on the shell (their corners carry no flux), the
+    // wrapped point on the periodic box (PER)
     auto fetch = [&](int gi, int gj, int kk) -> A {
-        if (gi < 0 || gi >= nr || gj < 0 || gj >= nt) return A(0);
+        if (gi < 0 || gi >= nr || gj < 0 || gj >= nt) {
+            if (!PER) return A(0);
+            gi = wrap_phi(gi, nr);
+            gj = wrap_phi(gj, nt);
+        }
         return ld(cg.offset + (long long)wrap_phi(kk, np) * plane + (long long)gj * nr + gi);
     };
     auto fetch_coef = [&](int ci, int cj, int kk) -> Coef4<A> {
-        const int gi = t.i0 - 1 + ci, gj = t.j0 - 1 + cj;
-        if (gi < 0 || gi >= nr || gj < 0 || gj >= nt) return Coef4<A>{A(0), A(0), A(0), A(0)};
+        int gi = t.i0 - 1 + ci, gj = t.j0 - 1 + cj;
+        if (gi < 0 || gi >= nr || gj < 0 || gj >= nt) {
+            if (!PER) return Coef4<A>{A(0), A(0), A(0), A(0)};
+            gi = wrap_phi(gi, nr);
+            gj = wrap_phi(gj, nt);
+        }
         return load_coef<A, typename P::C>(coef + cg.offset + (long long)wrap_phi(kk, np) * plane + (long long)gj * nr + gi);
     };
     // Corner (ci, cj) of the (TXv+1) x (TYv+1) corner grid from cell planes `pa` (k) and `pb` (k+1).
@@ -187,7 +197,7 @@ __device__ __forceinline__ void tc_tile(const CompGrid& cg, const TileIdx& t, co
 }
 
 // One-problem conduction march kernel (the register-prefetch path).
-template <class P, class Load, class Epi>
+template <class P, class Load, class Epi, bool PER = false>
 __global__ void __launch_bounds__(NTHREADS)
 tc_march(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld_in, Epi ep_in) {
     Epi ep = ep_in;
@@ -197,7 +207,7 @@ tc_march(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld_in,
     ld.init();
     const TileIdx t = decode_tile(g);
     __shared__ TileSmem<P, TX, TY> sm;
-    tc_tile<P, TX, TY>(g.c[0], t, coef, ld, ep, threadIdx.x + TX * threadIdx.y, sm);
+    tc_tile<P, TX, TY, Load, Epi, PER>(g.c[0], t, coef, ld, ep, threadIdx.x + TX * threadIdx.y, sm);
     ep.finish();
 }
 
@@ -208,7 +218,7 @@ tc_march(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld_in,
 // the four in-plane neighbours (other threads' points, served by L1 / L2) and prefetches the
 // next plane's operands one iteration ahead.
 // ---------------------------------------------------------------------------------------------
-template <class P, class Load, class Epi>
+template <class P, class Load, class Epi, bool PER = false>
 __global__ void __launch_bounds__(NTHREADS)
 visc_march(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld_in, Epi ep_in) {
     using A = typename P::A;
@@ -227,7 +237,10 @@ visc_march(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld_i
     const int i = t.i0 + threadIdx.x, j = t.j0 + threadIdx.y;
     const bool own = (i < nr) && (j < nt);
     if (own) {
-        const bool rm = i > 0, rp = i < nr - 1, tm = j > 0, tp = j < nt - 1;
+        // in-plane neighbours: absent past the r / theta ends of the shell, wrapped on the box (PER)
+        const bool rm = i > 0 || PER, rp = i < nr - 1 || PER, tm = j > 0 || PER, tp = j < nt - 1 || PER;
+        const int orm = PER && i == 0 ? nr - 1 : -1, orp = PER && i == nr - 1 ? -(nr - 1) : 1;
+        const int otm = PER && j == 0 ? (nt - 1) * nr : -nr, otp = PER && j == nt - 1 ? -(nt - 1) * nr : nr;
         const long long col = cg.offset + (long long)j * nr + i;
         auto at = [&](int kk) -> long long {
             kk = kk < 0 ? kk + np : (kk >= np ? kk - np : kk);
@@ -237,13 +250,13 @@ visc_march(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld_i
         struct Plane { A urm, urp, utm, utp, crm, ctm; Coef4<A> c; };
         auto fetch = [&](long long idx) -> Plane {
             Plane q;
-            q.urm = rm ? ld(idx - 1) : A(0);
-            q.urp = rp ? ld(idx + 1) : A(0);
-            q.utm = tm ? ld(idx - nr) : A(0);
-            q.utp = tp ? ld(idx + nr) : A(0);
+            q.urm = rm ? ld(idx + orm) : A(0);
+            q.urp = rp ? ld(idx + orp) : A(0);
+            q.utm = tm ? ld(idx + otm) : A(0);
+            q.utp = tp ? ld(idx + otp) : A(0);
             q.c = load_coef<A, C>(coef + idx);
-            q.crm = rm ? (A)__ldg(&coef[idx - 1].a) : A(0);
-            q.ctm = tm ? (A)__ldg(&coef[idx - nr].b) : A(0);
+            q.crm = rm ? (A)__ldg(&coef[idx + orm].a) : A(0);
+            q.ctm = tm ? (A)__ldg(&coef[idx + otm].b) : A(0);
             return q;
         };
         A ukm = ld(at(t.k0 - 1));

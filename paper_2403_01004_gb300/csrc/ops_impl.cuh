@@ -21,10 +21,14 @@ class OpsImpl : public Ops {
     static void march(Ctx& c, const void* coef, const Load& ld, const Epi& ep) {
         dim3 block(TX, TY);
         const Coef4<C>* cf = static_cast<const Coef4<C>*>(coef);
-        if (c.kind == PB_TC_ANISO)
-            tc_march<P, Load, Epi><<<c.grid.nblocks, block, 0, c.stream>>>(c.grid, cf, ld, ep);
-        else
-            visc_march<P, Load, Epi><<<c.grid.nblocks, block, 0, c.stream>>>(c.grid, cf, ld, ep);
+        const bool box = c.grid.c[0].periodic != 0;
+        if (c.kind == PB_TC_ANISO) {
+            if (box) tc_march<P, Load, Epi, true><<<c.grid.nblocks, block, 0, c.stream>>>(c.grid, cf, ld, ep);
+            else tc_march<P, Load, Epi><<<c.grid.nblocks, block, 0, c.stream>>>(c.grid, cf, ld, ep);
+        } else {
+            if (box) visc_march<P, Load, Epi, true><<<c.grid.nblocks, block, 0, c.stream>>>(c.grid, cf, ld, ep);
+            else visc_march<P, Load, Epi><<<c.grid.nblocks, block, 0, c.stream>>>(c.grid, cf, ld, ep);
+        }
         PB_CUDA_TRY(cudaGetLastError());
     }
 

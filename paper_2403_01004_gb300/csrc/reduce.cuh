@@ -67,7 +67,8 @@ __device__ __forceinline__ void block_argmax(double& v, long long& i) {
     if (lane == 0) { rv[warp] = v; ri[warp] = i; }
     __syncthreads();
     if (warp == 0) {
-        v = lane < nw ? rv[lane] : -1.0;
+        // empty lanes carry -inf, below any value a caller merges (|F| >= 0, or -bound)
+        v = lane < nw ? rv[lane] : -(1.0 / 0.0);
         i = lane < nw ? ri[lane] : 0x7fffffffffffffffLL;
         warp_argmax(v, i);
     }

@@ -70,9 +70,32 @@ __global__ void tc_coef_kernel(TCArgs a) {
     }
 }
 
+// Periodic box of unit cells (h = 1, W = V = 1), every corner present: record of point [i,j,k]
+// is ahat = sqrt(kappa_c) b / 4 of corner (i+1/2, j+1/2, k+1/2), kappa_c the mean of its 8 cells
+// (all indices wrap), and w = C / n.
+__global__ void tc_coef_box_kernel(TCArgs a) {
+    const long long n = (long long)a.nr * a.nt * a.np;
+    const long long pl = (long long)a.nr * a.nt;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % a.nr);
+        const long long q = t / a.nr;
+        const int j = (int)(q % a.nt);
+        const int k = (int)(q / a.nt);
+        const int i1 = (i + 1) % a.nr, j1 = (j + 1) % a.nt, k1 = (k + 1) % a.np;
+        const long long b0 = (long long)k * pl, b1 = (long long)k1 * pl;
+        const long long r0 = (long long)j * a.nr, r1 = (long long)j1 * a.nr;
+        const double kc = (a.kap[b0 + r0 + i] + a.kap[b0 + r0 + i1] + a.kap[b0 + r1 + i] + a.kap[b0 + r1 + i1]
+                         + a.kap[b1 + r0 + i] + a.kap[b1 + r0 + i1] + a.kap[b1 + r1 + i] + a.kap[b1 + r1 + i1]) / 8.0;
+        const double br = a.B0[t], bt = a.B1[t], bp = a.B2[t];
+        const double bm = sqrt(br * br + bt * bt + bp * bp);
+        const double root = sqrt(kc);
+        a.rec[t] = Coef4<double>{root * (br / bm) / 4.0, root * (bt / bm) / 4.0, root * (bp / bm) / 4.0, a.C / a.n[t]};
+    }
+}
+
 // Row of A at a cell from its 8 corners: A = -sum_c g_c g_c^T, g_c(p) = sigma(p) . ahat_c.
 // Writes diag(A) and the block maximum of w sum_j |A_ij| (the Gershgorin bound of L).
-__global__ void __launch_bounds__(256) tc_rows_kernel(int nr, int nt, int np, const Coef4<double>* rec,
+__global__ void __launch_bounds__(256) tc_rows_kernel(int nr, int nt, int np, int periodic, const Coef4<double>* rec,
                                                       double* adiag, double* part) {
     const long long n = (long long)nr * nt * np;
     const long long pl = (long long)nr * nt;
@@ -88,8 +111,13 @@ __global__ void __launch_bounds__(256) tc_rows_kernel(int nr, int nt, int np, co
 #pragma unroll
         for (int p = 0; p < 8; ++p) {
             const int pi = p & 1, pj = (p >> 1) & 1, pk = p >> 2;
-            const int ci = i - pi, cj = j - pj, ck = (k - pk + np) % np;
-            if (ci < 0 || cj < 0) continue;
+            int ci = i - pi, cj = j - pj;
+            const int ck = (k - pk + np) % np;
+            if (ci < 0 || cj < 0) {
+                if (!periodic) continue;
+                ci = (ci + nr) % nr;
+                cj = (cj + nt) % nt;
+            }
             const Coef4<double> c = rec[(long long)ck * pl + (long long)cj * nr + ci];
             const double gp = (2 * pi - 1) * c.a + (2 * pj - 1) * c.b + (2 * pk - 1) * c.c;
 #pragma unroll
@@ -178,8 +206,28 @@ __global__ void visc_coef_kernel(ViscArgs a) {
     }
 }
 
+// Periodic box of unit cells: every component on the full grid, c_f = nu_f rho_f on the +r,
+// +theta, +phi faces (means of the two points, indices wrapping; A_f = d_f = 1), w = 1/rho.
+__global__ void visc_coef_box_kernel(ViscArgs a) {
+    const long long n = (long long)a.nr * a.nt * a.np;
+    const long long pl = (long long)a.nr * a.nt;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % a.nr);
+        const long long q = t / a.nr;
+        const int j = (int)(q % a.nt);
+        const int k = (int)(q / a.nt);
+        const long long base = t - i - (long long)j * a.nr;     // start of plane k
+        const long long tr = base + (long long)j * a.nr + (i + 1) % a.nr;
+        const long long tt = base + (long long)((j + 1) % a.nt) * a.nr + i;
+        const long long tp = (long long)((k + 1) % a.np) * pl + (t - (long long)k * pl);
+        const double nu0 = a.nu[t], rho0 = a.rho[t];
+        auto face = [&](long long o) { return (0.5 * (nu0 + a.nu[o])) * (0.5 * (rho0 + a.rho[o])); };
+        a.rec[t] = Coef4<double>{face(tr), face(tt), face(tp), 1.0 / rho0};
+    }
+}
+
 // diag(A) = -sum of the six face coefficients; Gershgorin bound of L = 2 w sum_f c_f.
-__global__ void __launch_bounds__(256) visc_rows_kernel(int nr, int nt, int np, const Coef4<double>* rec,
+__global__ void __launch_bounds__(256) visc_rows_kernel(int nr, int nt, int np, int periodic, const Coef4<double>* rec,
                                                         double* adiag, double* part) {
     const long long n = (long long)nr * nt * np;
     const long long pl = (long long)nr * nt;
@@ -192,7 +240,9 @@ __global__ void __launch_bounds__(256) visc_rows_kernel(int nr, int nt, int np, 
         const Coef4<double> c = rec[t];
         double s = c.a + c.b + c.c;
         if (i > 0) s += rec[t - 1].a;
+        else if (periodic) s += rec[t + nr - 1].a;
         if (j > 0) s += rec[t - nr].b;
+        else if (periodic) s += rec[t + (long long)(nt - 1) * nr].b;
         s += rec[(long long)((k + np - 1) % np) * pl + (t - (long long)k * pl)].c;
         adiag[t] = -s;
         gmax = fmax(gmax, 2.0 * c.w * s);
@@ -229,6 +279,7 @@ int reduce_blocks(const Ctx& c) { return setup_blocks(c, c.n); }
 // Copies the face arrays (conduction) or the per-component point / bound arrays (viscosity) to
 // the device once per context.
 void setup_geometry(Ctx& c, const pb_grid& g) {
+    if (c.geometry == PB_CARTESIAN_PERIODIC) return;     // unit cells: no metric arrays
     const int nr = g.n_r, nt = g.n_theta;
     std::vector<double> rf(g.r_face, g.r_face + nr + 1), tf(g.t_face, g.t_face + nt + 1);
     if (c.kind == PB_TC_ANISO) {
@@ -258,10 +309,12 @@ void setup_tc(Ctx& c, const pb_operator& op, Coef4<double>* rec, double* dt_e) {
     const int blocks = setup_blocks(c, n);
     kappa_kernel<<<blocks, 256, 0, c.stream>>>(n, op.T0, kap);
     TCArgs a{c.nr, c.nt, c.np, 2.0 * M_PI / c.np, op.C, c.geo[0], c.geo[1], kap, op.n, op.B[0], op.B[1], op.B[2], rec};
-    tc_coef_kernel<<<blocks, 256, 0, c.stream>>>(a);
+    const bool box = c.geometry == PB_CARTESIAN_PERIODIC;
+    if (box) tc_coef_box_kernel<<<blocks, 256, 0, c.stream>>>(a);
+    else tc_coef_kernel<<<blocks, 256, 0, c.stream>>>(a);
     double* part = static_cast<double*>(c.partials);
     double* adiag = c.s64;   // kappa is no longer needed
-    tc_rows_kernel<<<blocks, 256, 0, c.stream>>>(c.nr, c.nt, c.np, rec, adiag, part);
+    tc_rows_kernel<<<blocks, 256, 0, c.stream>>>(c.nr, c.nt, c.np, box ? 1 : 0, rec, adiag, part);
     max_finalize_kernel<<<1, 256, 0, c.stream>>>(part, blocks, c.d_scalar);
     PB_CUDA_TRY(cudaGetLastError());
     PB_CUDA_TRY(cudaMemcpyAsync(c.h_scalar, c.d_scalar, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
@@ -279,9 +332,10 @@ void setup_visc(Ctx& c, const pb_operator& op, Coef4<double>* rec, double* dt_e)
         ViscArgs a{cg.nr, cg.nt, cg.np, 2.0 * M_PI / c.np, c.geo[4 * comp], c.geo[4 * comp + 1], c.geo[4 * comp + 2],
                    c.geo[4 * comp + 3], op.rho[comp], op.nu[comp], rec + cg.offset};
         const int blocks = setup_blocks(c, n);
-        visc_coef_kernel<<<blocks, 256, 0, c.stream>>>(a);
-        visc_rows_kernel<<<blocks, 256, 0, c.stream>>>(cg.nr, cg.nt, cg.np, rec + cg.offset, adiag + cg.offset,
-                                                       part + total_blocks);
+        if (cg.periodic) visc_coef_box_kernel<<<blocks, 256, 0, c.stream>>>(a);
+        else visc_coef_kernel<<<blocks, 256, 0, c.stream>>>(a);
+        visc_rows_kernel<<<blocks, 256, 0, c.stream>>>(cg.nr, cg.nt, cg.np, cg.periodic, rec + cg.offset,
+                                                       adiag + cg.offset, part + total_blocks);
         total_blocks += blocks;
     }
     max_finalize_kernel<<<1, 256, 0, c.stream>>>(part, total_blocks, c.d_scalar);

@@ -3,6 +3,7 @@
 On such a box the oracle operators reduce to constant-coefficient stencils whose Fourier symbols
 are known in closed form.  These helpers only build coefficient arrays for the oracle classes."""
 import numpy as np
+from scipy.special import eval_gegenbauer, eval_legendre
 
 from oracle.tc import TCOperator
 from oracle.visc import ViscOperator
@@ -42,3 +43,15 @@ def tc_symbol(th, bhat, kappa=1.0):
 
 def visc_symbol(th):
     return -sum(4 * np.sin(t / 2) ** 2 for t in th)
+
+
+def R_closed(scheme, s, z):
+    """Amplification factor of s-stage RKL2 (shifted Legendre form) or RKG2 (Gegenbauer C^(3/2)
+    form, Appendix A) at z = dt lambda, written from the closed forms of the stability
+    polynomials: R = a_s + b_s P(1 + w z)."""
+    if scheme == "rkl2":
+        b = (s * s + s - 2.0) / (2.0 * s * (s + 1.0))
+        return (1 - b) + b * eval_legendre(s, 1.0 + 4.0 / (s * s + s - 2.0) * z)
+    b = 4.0 * (s - 1.0) * (s + 4.0) / (3.0 * s * (s + 1.0) * (s + 2.0) * (s + 3.0))
+    a = 1.0 - b * (s + 1.0) * (s + 2.0) / 2.0
+    return a + b * eval_gegenbauer(s, 1.5, 1.0 + 6.0 / ((s + 4.0) * (s - 1.0)) * z)

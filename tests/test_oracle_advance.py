@@ -18,16 +18,7 @@ from oracle.ptl import ptl, ptl_full
 from oracle.sts import rkg2_stages, rkl2_stages
 from oracle.tc import TCOperator
 from oracle.visc import ViscOperator
-from periodic import mode, tc_box, tc_symbol, visc_box, visc_symbol
-
-
-def R_closed(scheme, s, z):
-    if scheme == "rkl2":
-        b = (s * s + s - 2.0) / (2.0 * s * (s + 1.0))
-        return (1 - b) + b * eval_legendre(s, 1.0 + 4.0 / (s * s + s - 2.0) * z)
-    b = 4.0 * (s - 1.0) * (s + 4.0) / (3.0 * s * (s + 1.0) * (s + 2.0) * (s + 3.0))
-    a = 1.0 - b * (s + 1.0) * (s + 2.0) / 2.0
-    return a + b * eval_gegenbauer(s, 1.5, 1.0 + 6.0 / ((s + 4.0) * (s - 1.0)) * z)
+from periodic import R_closed, mode, tc_box, tc_symbol, visc_box, visc_symbol
 
 
 STAGES = {"rkl2": rkl2_stages, "rkg2": rkg2_stages}
