@@ -57,6 +57,9 @@ def parse_args():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-launch sub-benchmark")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-guess sub-benchmark")
     ap.add_argument("--no-rkg2", action="store_true", help="skip the RKG2 comparison step")
+    ap.add_argument("--no-ptl-study", action="store_true", help="skip the F_max vs full-grid PTL study")
+    ap.add_argument("--no-stress", action="store_true", help="skip the jump128 precision-stress probe")
+    ap.add_argument("--no-fig1", action="store_true", help="skip the Fig. 1 reproduction on the periodic box")
     return ap.parse_args()
 
 
@@ -293,6 +296,12 @@ def run_ours(args):
         args.scheme = prev
         extra["rkg2_step"] = {"value": units_g / (ms_g / 1e3), "unit": UNIT, "ms_per_step": ms_g,
                               "step": {k: dict(cycles=v_["cycles"], stages=v_["total_stages"]) for k, v_ in stats.items()}}
+    if not args.no_ptl_study:
+        extra["ptl_study"] = ptl_study_probe(pb, torch, ctx_tc, ctx_v, d_u0, d_v0, wl)
+    if not args.no_stress:
+        extra["precision_stress"] = precision_stress_probe(pb, torch)
+    if not args.no_fig1:
+        extra["fig1"] = fig1_probe(pb, torch)
     if not args.no_pcg:
         extra["pcg"] = pcg_probe(pb, torch, g, d_tc, d_u0, wl)
     if not args.no_batch:
@@ -491,6 +500,156 @@ def learned_probe(pb, torch):
                          "generate_s": round(t_gen, 2), "steps": 1000, "train_s": round(t_train, 2),
                          "last_batch_loss": loss},
             **out}
+
+
+def ptl_study_probe(pb, torch, ctx_tc, ctx_v, d_u0, d_v0, wl):
+    """The F_max localisation of Eq. 5 against the full-grid PTL (Eq. 4 over every pair of face
+    neighbours) on the step's own states: both values before every cycle of the Eq. 5 step, the
+    same step cycled by the full-grid value instead, and the full-grid pass's own rate."""
+    import numpy as np
+    out = {"what": "RKL2 step of each operator (dt = %g dt_E), float32: Eq. 5 (F_max) vs Eq. 4 over all "
+                   "pairs (full), both evaluated before every cycle of the Eq. 5-driven step" % wl["ratio"]}
+    for name, ctx, src in (("tc", ctx_tc, d_u0), ("visc", ctx_v, d_v0)):
+        dte = pb.parabolic_dt_explicit(ctx)
+        dt = wl["ratio"] * dte
+        x = src.clone()
+        st = pb.rkl2_advance(ctx, x, dt, use_ptl=True, record_full=True, stats_capacity=8192)
+        fm = np.array(st["dt_ptl_cycle"], dtype=np.float64)
+        fu = np.array(st["dt_full_cycle"], dtype=np.float64)
+        ok = np.isfinite(fm) & np.isfinite(fu) & (fm > 0)
+        r = fu[ok] / fm[ok]
+        rec = {"cycles": st["cycles"], "stages": st["total_stages"],
+               "full_below_fmax_by_0.1pct": float(np.mean(r < 0.999)) if r.size else None,
+               "full_below_half_fmax": float(np.mean(r < 0.5)) if r.size else None,
+               "ratio_full_over_fmax": {"min": float(r.min()), "median": float(np.median(r)), "max": float(r.max())}
+               if r.size else None,
+               "fmax_over_dtE": {"first": float(fm[0] / dte), "median": float(np.median(fm[ok]) / dte)},
+               "full_over_dtE": {"first": float(fu[0] / dte), "median": float(np.median(fu[ok]) / dte)}}
+        x = src.clone()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st2 = pb.rkl2_advance(ctx, x, dt, use_ptl=True, ptl_mode="full", raise_on_error=False)
+        e1.record()
+        torch.cuda.synchronize()
+        rec["cycled_by_full"] = {"status": st2["status"], "cycles": st2["cycles"], "stages": st2["total_stages"],
+                                 "ms": e0.elapsed_time(e1)}
+        out[name] = rec
+    # the full-grid pass alone (after its PTL pass), event-timed per launch
+    pb.pb_profile_enable(ctx_tc, True)
+    for _ in range(5):
+        pb.ptl_full_compute(ctx_tc, d_u0)
+    torch.cuda.synchronize()
+    prof = {p["name"]: p for p in pb.pb_profile_read(ctx_tc)}
+    pb.pb_profile_enable(ctx_tc, False)
+    p = prof.get("tc.ptl_full")
+    if p and p["timed_launches"]:
+        ms = p["total_ms"] / p["timed_launches"]
+        out["ptl_full_pass"] = {"ms_per_launch": round(ms, 4), "alg_bytes": p["bytes"] / p["launches"],
+                                "GB/s": round(p["bytes"] / p["launches"] / (ms / 1e3) / 1e9, 1)}
+    return out
+
+
+def fig1_probe(pb, torch, n_phi=256, ratio=500.0):
+    """Fig. 1 on the GPU.  Middle / right: the 1-D second-order heat equation at 500 explicit
+    steps is the periodic conduction box 3 x 3 x n_phi with the field along phi (dt_E = 1/2 for
+    states constant in r and theta); one step from a delta plane carries every mode, and the FFT
+    along phi gives each mode's amplification, z_m = -1000 sin^2(pi m / n_phi).  Left: the
+    estimated speedup over explicit Euler, (dt / dt_E) / s, from the library's stage counts."""
+    import numpy as np
+    from scipy.special import eval_gegenbauer, eval_legendre
+
+    def closed(scheme, s, z):
+        if scheme == "rkl2":
+            b = (s * s + s - 2.0) / (2.0 * s * (s + 1.0))
+            return (1 - b) + b * eval_legendre(s, 1.0 + 4.0 / (s * s + s - 2.0) * z)
+        b = 4.0 * (s - 1.0) * (s + 4.0) / (3.0 * s * (s + 1.0) * (s + 2.0) * (s + 3.0))
+        return 1.0 - b * (s + 1.0) * (s + 2.0) / 2.0 + b * eval_gegenbauer(s, 1.5, 1.0 + 6.0 / ((s + 4.0) * (s - 1.0)) * z)
+
+    shape = (n_phi, 3, 3)
+    ones = torch.ones(shape, dtype=torch.float64, device="cuda")
+    fields = {"T0": ones, "n": ones, "B": [0 * ones, 0 * ones, ones]}
+    ctx = pb.parabolic_setup_box(3, 3, n_phi, "tc", fields, "fp64", C=1.0)
+    dt_e = pb.parabolic_dt_explicit(ctx)
+    m = np.arange(n_phi)
+    z = ratio * dt_e * (-4.0 * np.sin(np.pi * m / n_phi) ** 2)
+    high = np.abs(z) > 0.5 * np.abs(z).max()
+    out = {"what": "1-D heat equation (box 3x3x%d, field along phi), one step of %g dt_E from a delta plane; "
+                   "amplification per Fourier mode" % (n_phi, ratio), "dt_E": dt_e, "z_min": float(z.min())}
+    for scheme in ("rkl2", "rkg2", "be"):
+        u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+        u[0] = 1.0
+        u = u.reshape(-1)
+        if scheme == "be":
+            st = pb.be_pcg_advance(ctx, u, ratio * dt_e, use_ptl=False, rtol=1e-14, max_iter=20000)
+            ref, s = 1.0 / (1.0 - z), None
+        else:
+            st = pb.rkl2_advance(ctx, u, ratio * dt_e, scheme=scheme, use_ptl=False)
+            s = st["work_cycle"][0]
+            ref = closed(scheme, s, z)
+        amp = np.fft.fft(u.reshape(shape)[:, 1, 1].cpu().numpy()).real
+        out[scheme] = {"stages": s, "pcg_iterations": st["total_iters"] if scheme == "be" else None,
+                       "max_abs_amp_high_modes": float(np.abs(amp[high]).max()),
+                       "spread_high_modes": float(np.ptp(amp[high])),
+                       "max_dev_from_closed_form": float(np.abs(amp - ref).max())}
+    out["exact_max_high_modes"] = float(np.exp(z[high]).max())
+    speed = {}
+    for r in (10.0, 30.0, 100.0, 300.0, 1000.0, 3000.0, 1e4, 3e4, 1e5):
+        row = {}
+        for scheme in ("rkl2", "rkg2"):
+            u = torch.zeros(shape[0] * 9, dtype=torch.float64, device="cuda")
+            st = pb.rkl2_advance(ctx, u, r * dt_e, scheme=scheme, use_ptl=False)
+            row[scheme] = round(r / st["work_cycle"][0], 3)
+        speed["%g" % r] = row
+    out["estimated_speedup_vs_euler"] = speed
+    ctx.close()
+    return out
+
+
+def precision_stress_probe(pb, torch, bf16_cap=5000):
+    """The jump128 workload (128 x 256 x 512 shell, temperature jump at r = 1.02 over three radial
+    cells, 5 % noise; RKL2 + PTL over dt = 1e5 dt_E) in float64, float32 and bfloat16 storage:
+    each precision's own PTL schedule (cycles, stages, time; bfloat16 capped at bf16_cap cycles),
+    and its error against the float64 oracle's sampled final state when it replays the oracle's
+    schedule (tests/golden/jump128_rkl2_ptl.txt, written by the oracle-only script beside it)."""
+    import importlib.util
+    import numpy as np
+    import synth
+    from synth import device
+    spec = importlib.util.spec_from_file_location("jump128_golden", os.path.join(ROOT, "tests", "jump128_golden.py"))
+    golden = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(golden)
+    if not os.path.exists(golden.PATH):
+        return {"unavailable": "tests/golden/jump128_rkl2_ptl.txt missing"}
+    gold = golden.load()
+    wl = synth.WORKLOADS["jump128"]
+    g = synth.make_grid(wl["n_r"], wl["n_t"], wl["n_p"], wl["q"])
+    inp = synth.tc_inputs(g, wl["seed"], noise=wl["noise"], profile="jump")
+    fields = device.tc_fields(inp)
+    idx = torch.from_numpy(gold["idx"]).to("cuda")
+    out = {"what": "jump128: 128x256x512 shell, T jump at r = 1.02 (3 cells), RKL2 + PTL over 1e5 dt_E",
+           "oracle": {"cycles": len(gold["dt_c"]), "stages": int(sum(gold["s"]))}}
+    for prec, dtype in (("fp64", torch.float64), ("fp32", torch.float32), ("bf16", torch.bfloat16)):
+        ctx = pb.parabolic_setup(g.r_face, g.t_face, g.n_phi, "tc", fields, prec)
+        dt = wl["ratio"] * pb.parabolic_dt_explicit(ctx)
+        rec = {}
+        for mode in ("own_ptl", "oracle_schedule"):
+            u = torch.from_numpy(inp.T.reshape(-1)).to("cuda", dtype)
+            kw = dict(use_ptl=True, max_cycles=bf16_cap) if mode == "own_ptl" else dict(forced=gold["dt_c"])
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = pb.rkl2_advance(ctx, u, dt, raise_on_error=False, **kw)
+            e1.record()
+            torch.cuda.synchronize()
+            got = u[idx].to(torch.float64).cpu().numpy()
+            err = float(np.linalg.norm(got - gold["u"]) / np.linalg.norm(gold["u"]))
+            rec[mode] = {"status": pb.load_library().pb_status_string(st["status"]).decode(),
+                         "cycles": st["cycles"], "stages": st["total_stages"], "ms": round(e0.elapsed_time(e1), 2),
+                         "sampled_rel_l2_vs_oracle": err}
+        out[prec] = rec
+        ctx.close()
+    return out
 
 
 def fp64_probe(pb, torch, g, d_tc, d_vi, d_u0, d_v0, wl, args, value32):

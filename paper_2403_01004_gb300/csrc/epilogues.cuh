@@ -428,42 +428,62 @@ ptl_finalize_kernel(MarchGrid g, const typename P::S* u, const typename P::S* F,
 // dF = F_i - F_j != 0 and du dF < 0 bounds dt by -du/dF (arithmetic precision).  Each block
 // leaves the smallest bound and, among equal bounds, the smallest key 3 i + d, as an ArgMax of
 // -bound (-inf when no pair qualifies).
+template <typename A> struct Eps;
+template <> struct Eps<float> { static constexpr float value = 1.1920929e-7f; };
+template <> struct Eps<double> { static constexpr double value = 2.220446049250313e-16; };
+
 template <class P>
 __global__ void __launch_bounds__(256)
 ptl_full_kernel(MarchGrid g, long long n, const typename P::S* u, const typename P::S* F, ArgMax* part) {
     using A = typename P::A;
     A best = A(0);
     long long key = LLONG_MAX;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-        int comp = 0;
-        for (int c = 1; c < g.ncomp; ++c)
-            if (t >= g.c[c].offset) comp = c;
-        const CompGrid& cg = g.c[comp];
-        const long long loc = t - cg.offset;
+    // rows of constant (component, phi, theta): a warp walks a row along r (coalesced), so the
+    // flat index is decoded once per row instead of once per point
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long w0 = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    long long rows_before = 0;
+    for (int c = 0; c < g.ncomp; ++c) {
+        const CompGrid& cg = g.c[c];
         const long long plane = (long long)cg.nr * cg.nt;
-        const long long kk = loc / plane;
-        const long long rem = loc - kk * plane;
-        const int j = (int)(rem / cg.nr);
-        const int i = (int)(rem - (long long)j * cg.nr);
-        const A ut = cvt<A>(u[t]), ft = cvt<A>(F[t]);
-        auto pair = [&](long long q, int d) {
-            const A du = ut - cvt<A>(u[q]);
-            const A df = ft - cvt<A>(F[q]);
-            if (du != A(0) && df != A(0) && du * df < A(0)) {
-                const A b = -du / df;
-                const long long kq = 3 * t + d;
-                if (key == LLONG_MAX || b < best || (b == best && kq < key)) {
-                    best = b;
-                    key = kq;
-                }
+        const long long rows = (long long)cg.nt * cg.np;
+        // this warp's first row of the component in the global row sequence
+        long long r = w0 - rows_before;
+        if (r < 0) r += ((-r + warps - 1) / warps) * warps;
+        for (; r < rows; r += warps) {
+            const int kk = (int)(r / cg.nt);
+            const int j = (int)(r - (long long)kk * cg.nt);
+            const long long row = cg.offset + (long long)kk * plane + (long long)j * cg.nr;
+            const long long up_t = j + 1 < cg.nt ? (long long)cg.nr : (cg.periodic ? -(long long)(cg.nt - 1) * cg.nr : 0);
+            const long long up_p = kk + 1 < cg.np ? plane : -(long long)(cg.np - 1) * plane;
+            for (int i = lane; i < cg.nr; i += 32) {
+                const long long t = row + i;
+                const A ut = cvt<A>(u[t]), ft = cvt<A>(F[t]);
+                auto pair = [&](long long q, int d) {
+                    const A du = ut - cvt<A>(u[q]);
+                    const A df = ft - cvt<A>(F[q]);
+                    if (du != A(0) && df != A(0) && du * df < A(0)) {
+                        // b = |du| / |dF| can only reach `best` if |du| <= best |dF| (1 + 4 eps):
+                        // a multiply rules out most pairs before the (exact) division
+                        if (key != LLONG_MAX && fabs(du) > best * fabs(df) * (A(1) + A(4) * Eps<A>::value)) return;
+                        const A b = -du / df;
+                        const long long kq = 3 * t + d;
+                        if (key == LLONG_MAX || b < best || (b == best && kq < key)) {
+                            best = b;
+                            key = kq;
+                        }
+                    }
+                };
+                if (i + 1 < cg.nr) pair(t + 1, 0);
+                else if (cg.periodic) pair(t - (cg.nr - 1), 0);
+                if (up_t != 0) pair(t + up_t, 1);
+                pair(t + up_p, 2);
             }
-        };
-        if (i + 1 < cg.nr) pair(t + 1, 0);
-        else if (cg.periodic) pair(t - (cg.nr - 1), 0);
-        if (j + 1 < cg.nt) pair(t + cg.nr, 1);
-        else if (cg.periodic) pair(t - (long long)(cg.nt - 1) * cg.nr, 1);
-        pair(kk + 1 < cg.np ? t + plane : cg.offset + rem, 2);
+        }
+        rows_before += rows;
     }
+    (void)n;
     double v = key == LLONG_MAX ? -(1.0 / 0.0) : -(double)best;
     block_argmax(v, key);
     if (threadIdx.x == 0) part[blockIdx.x] = ArgMax{v, key};
