@@ -30,43 +30,57 @@ struct TCArgs {
     Coef4<double>* rec;
 };
 
+// phi planes per thread in the record kernels: a thread owns one (r, theta) column and a chunk of
+// planes, so the metric factors (independent of phi; cosines, sines, divisions in float64) are
+// formed once per chunk, not once per point
+constexpr int kPlaneChunk = 32;
+
 // Record of point [i,j,k]: ahat of corner (i+1/2, j+1/2, k+1/2) and w = C/(n V) of cell (i,j,k).
 //   ahat = sqrt(W kappa_c) (h_r b_r, h_t b_t, h_p b_p) / 4,  kappa_c = mean of the 8 cells,
 //   h_r = 1/(rc[i+1]-rc[i]), h_t = 1/(rf[i+1] (tc[j+1]-tc[j])), h_p = 1/(rf[i+1] sin tf[j+1] dphi),
 //   W = rf[i+1]^2 (rc[i+1]-rc[i]) sin tf[j+1] (tc[j+1]-tc[j]) dphi, b = B/|B| at the corner.
 __global__ void tc_coef_kernel(TCArgs a) {
-    const long long n = (long long)a.nr * a.nt * a.np;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(t % a.nr);
-        const long long q = t / a.nr;
-        const int j = (int)(q % a.nt);
-        const int k = (int)(q / a.nt);
+    const long long pl = (long long)a.nr * a.nt;
+    const int nchunk = (a.np + kPlaneChunk - 1) / kPlaneChunk;
+    const long long total = pl * nchunk;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
+        const long long col = w % pl;
+        const int q = (int)(w / pl);
+        const int i = (int)(col % a.nr);
+        const int j = (int)(col / a.nr);
         const double V = (a.rf[i + 1] * a.rf[i + 1] * a.rf[i + 1] - a.rf[i] * a.rf[i] * a.rf[i]) / 3.0
                        * (cos(a.tf[j]) - cos(a.tf[j + 1])) * a.dphi;
-        Coef4<double> r{0.0, 0.0, 0.0, a.C / (a.n[t] * V)};
-        if (i < a.nr - 1 && j < a.nt - 1) {
-            const int k1 = (k + 1) % a.np;
-            const long long pl = (long long)a.nr * a.nt;
-            const long long b0 = (long long)k * pl, b1 = (long long)k1 * pl;
-            const long long r0 = (long long)j * a.nr + i, r1 = (long long)(j + 1) * a.nr + i;
-            const double kc = (a.kap[b0 + r0] + a.kap[b0 + r0 + 1] + a.kap[b0 + r1] + a.kap[b0 + r1 + 1]
-                             + a.kap[b1 + r0] + a.kap[b1 + r0 + 1] + a.kap[b1 + r1] + a.kap[b1 + r1 + 1]) / 8.0;
+        const bool corner = i < a.nr - 1 && j < a.nt - 1;
+        double hr = 0.0, ht = 0.0, hp = 0.0, W = 0.0;
+        if (corner) {
             const double rci = 0.5 * (a.rf[i] + a.rf[i + 1]), rcp = 0.5 * (a.rf[i + 1] + a.rf[i + 2]);
             const double tci = 0.5 * (a.tf[j] + a.tf[j + 1]), tcp = 0.5 * (a.tf[j + 1] + a.tf[j + 2]);
             const double drc = rcp - rci, dtc = tcp - tci;
             const double rfc = a.rf[i + 1], stf = sin(a.tf[j + 1]);
-            const double hr = 1.0 / drc;
-            const double ht = 1.0 / (rfc * dtc);
-            const double hp = 1.0 / (rfc * stf * a.dphi);
-            const double W = rfc * rfc * drc * (stf * dtc) * a.dphi;
-            const double br = a.B0[t], bt = a.B1[t], bp = a.B2[t];
-            const double bm = sqrt(br * br + bt * bt + bp * bp);
-            const double root = sqrt(W * kc);
-            r.a = root * hr * (br / bm) / 4.0;
-            r.b = root * ht * (bt / bm) / 4.0;
-            r.c = root * hp * (bp / bm) / 4.0;
+            hr = 1.0 / drc;
+            ht = 1.0 / (rfc * dtc);
+            hp = 1.0 / (rfc * stf * a.dphi);
+            W = rfc * rfc * drc * (stf * dtc) * a.dphi;
         }
-        a.rec[t] = r;
+        const long long r0 = (long long)j * a.nr + i, r1 = (long long)(j + 1) * a.nr + i;
+        const int k_end = min(a.np, (q + 1) * kPlaneChunk);
+        for (int k = q * kPlaneChunk; k < k_end; ++k) {
+            const long long t = (long long)k * pl + col;
+            Coef4<double> r{0.0, 0.0, 0.0, a.C / (a.n[t] * V)};
+            if (corner) {
+                const int k1 = (k + 1) % a.np;
+                const long long b0 = (long long)k * pl, b1 = (long long)k1 * pl;
+                const double kc = (a.kap[b0 + r0] + a.kap[b0 + r0 + 1] + a.kap[b0 + r1] + a.kap[b0 + r1 + 1]
+                                 + a.kap[b1 + r0] + a.kap[b1 + r0 + 1] + a.kap[b1 + r1] + a.kap[b1 + r1 + 1]) / 8.0;
+                const double br = a.B0[t], bt = a.B1[t], bp = a.B2[t];
+                const double bm = sqrt(br * br + bt * bt + bp * bp);
+                const double root = sqrt(W * kc);
+                r.a = root * hr * (br / bm) / 4.0;
+                r.b = root * ht * (bt / bm) / 4.0;
+                r.c = root * hp * (bp / bm) / 4.0;
+            }
+            a.rec[t] = r;
+        }
     }
 }
 
@@ -119,13 +133,17 @@ __global__ void __launch_bounds__(256) tc_rows_kernel(int nr, int nt, int np, in
                 cj = (cj + nt) % nt;
             }
             const Coef4<double> c = rec[(long long)ck * pl + (long long)cj * nr + ci];
-            const double gp = (2 * pi - 1) * c.a + (2 * pj - 1) * c.b + (2 * pk - 1) * c.c;
+            // g(q) = sigma(q) . ahat for the corner's 8 cells, from the 4 (r, theta) sign sums
+            const double e[4] = {-c.a - c.b, c.a - c.b, -c.a + c.b, c.a + c.b};
+            double g[8];
 #pragma unroll
-            for (int p2 = 0; p2 < 8; ++p2) {
-                const int qi = p2 & 1, qj = (p2 >> 1) & 1, qk = p2 >> 2;
-                const double gq = (2 * qi - 1) * c.a + (2 * qj - 1) * c.b + (2 * qk - 1) * c.c;
+            for (int q = 0; q < 8; ++q) g[q] = e[q & 3] + (q >= 4 ? c.c : -c.c);
+            const double gp = g[p];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int qi = q & 1, qj = (q >> 1) & 1, qk = q >> 2;
                 const int o = (qi - pi + 1) + 3 * (qj - pj + 1) + 9 * (qk - pk + 1);
-                acc[o] -= gp * gq;
+                acc[o] -= gp * g[q];
             }
         }
         double s = 0.0;
@@ -172,37 +190,43 @@ struct ViscArgs {
 };
 
 // Record of point [i,j,k]: c_f = A_f nu_f rho_f / d_f on its +r, +theta, +phi faces (means of the
-// two points for nu and rho; zero past the last r / theta point) and w = 1/(rho V).
+// two points for nu and rho; zero past the last r / theta point) and w = 1/(rho V).  One thread
+// per (r, theta) column and chunk of phi planes, as for conduction.
 __global__ void visc_coef_kernel(ViscArgs a) {
-    const long long n = (long long)a.nr * a.nt * a.np;
     const long long pl = (long long)a.nr * a.nt;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(t % a.nr);
-        const long long q = t / a.nr;
-        const int j = (int)(q % a.nt);
-        const int k = (int)(q / a.nt);
+    const int nchunk = (a.np + kPlaneChunk - 1) / kPlaneChunk;
+    const long long total = pl * nchunk;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
+        const long long col = w % pl;
+        const int q = (int)(w / pl);
+        const int i = (int)(col % a.nr);
+        const int j = (int)(col / a.nr);
         const double dcos = cos(a.et[j]) - cos(a.et[j + 1]);
         const double dr2 = (a.er[i + 1] * a.er[i + 1] - a.er[i] * a.er[i]) / 2.0;
         const double V = (a.er[i + 1] * a.er[i + 1] * a.er[i + 1] - a.er[i] * a.er[i] * a.er[i]) / 3.0 * dcos * a.dphi;
-        const double nu0 = a.nu[t], rho0 = a.rho[t];
-        Coef4<double> r{0.0, 0.0, 0.0, 1.0 / (rho0 * V)};
+        double gr = 0.0, gt = 0.0;   // A_f / d_f of the +r and +theta faces
         if (i < a.nr - 1) {
             const double A = a.er[i + 1] * a.er[i + 1] * dcos * a.dphi;
             const double d = a.pr[i + 1] - a.pr[i];
-            r.a = (A / d) * ((0.5 * (nu0 + a.nu[t + 1])) * (0.5 * (rho0 + a.rho[t + 1])));
+            gr = A / d;
         }
         if (j < a.nt - 1) {
             const double A = dr2 * sin(a.et[j + 1]) * a.dphi;
             const double d = a.pr[i] * (a.pt[j + 1] - a.pt[j]);
-            r.b = (A / d) * ((0.5 * (nu0 + a.nu[t + a.nr])) * (0.5 * (rho0 + a.rho[t + a.nr])));
+            gt = A / d;
         }
-        {
-            const long long tk = (long long)((k + 1) % a.np) * pl + (t - (long long)k * pl);
-            const double A = dr2 * (a.et[j + 1] - a.et[j]);
-            const double d = a.pr[i] * sin(a.pt[j]) * a.dphi;
-            r.c = (A / d) * ((0.5 * (nu0 + a.nu[tk])) * (0.5 * (rho0 + a.rho[tk])));
+        const double gp = (dr2 * (a.et[j + 1] - a.et[j])) / (a.pr[i] * sin(a.pt[j]) * a.dphi);
+        const int k_end = min(a.np, (q + 1) * kPlaneChunk);
+        for (int k = q * kPlaneChunk; k < k_end; ++k) {
+            const long long t = (long long)k * pl + col;
+            const double nu0 = a.nu[t], rho0 = a.rho[t];
+            Coef4<double> r{0.0, 0.0, 0.0, 1.0 / (rho0 * V)};
+            if (i < a.nr - 1) r.a = gr * ((0.5 * (nu0 + a.nu[t + 1])) * (0.5 * (rho0 + a.rho[t + 1])));
+            if (j < a.nt - 1) r.b = gt * ((0.5 * (nu0 + a.nu[t + a.nr])) * (0.5 * (rho0 + a.rho[t + a.nr])));
+            const long long tk = (long long)((k + 1) % a.np) * pl + col;
+            r.c = gp * ((0.5 * (nu0 + a.nu[tk])) * (0.5 * (rho0 + a.rho[tk])));
+            a.rec[t] = r;
         }
-        a.rec[t] = r;
     }
 }
 
