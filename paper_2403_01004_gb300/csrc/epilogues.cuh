@@ -365,9 +365,12 @@ pcg_update_f32x4_kernel(long long n, float* x, float* r, const float* p, const f
     pcg_update_finish(acc, sc, part, counter);
 }
 
-// PTL (Eq. 5) at k = argmax |F| over the block partials; one block.
+// PTL (Eq. 5) at k = argmax |F| over the block partials; one block of up to kFinalizeThreads
+// (a march launch leaves thousands of partials: more threads shorten each one's chain of loads).
+constexpr int kFinalizeThreads = 1024;
+
 template <class P>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kFinalizeThreads)
 ptl_finalize_kernel(MarchGrid g, const typename P::S* u, const typename P::S* F,
                     const ArgMax* part, int nparts, PtlResult* res, const int* nonfinite) {
     using A = typename P::A;
@@ -490,7 +493,7 @@ ptl_full_kernel(MarchGrid g, long long n, const typename P::S* u, const typename
 }
 
 // One block: the smallest bound over the partials of ptl_full_kernel into res->dt_full / key_full.
-static __global__ void __launch_bounds__(256)
+static __global__ void __launch_bounds__(kFinalizeThreads)
 ptl_full_finalize_kernel(const ArgMax* part, int nparts, PtlResult* res) {
     double v = -(1.0 / 0.0);
     long long i = LLONG_MAX;

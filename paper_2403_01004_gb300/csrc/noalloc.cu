@@ -105,7 +105,7 @@ int run(const MarchGrid& g, int kind, const void* rec, const void* u, void* F, u
         tc_march<P, LoadState<P>, EpiF<P, true, false>><<<g.nblocks, dim3(TX, TY), 0, s>>>(g, cf, ld, ep);
     else
         visc_march<P, LoadState<P>, EpiF<P, true, false>><<<g.nblocks, dim3(TX, TY), 0, s>>>(g, cf, ld, ep);
-    ptl_finalize_kernel<P><<<1, 256, 0, s>>>(g, static_cast<const S*>(u), static_cast<const S*>(F), part,
+    ptl_finalize_kernel<P><<<1, kFinalizeThreads, 0, s>>>(g, static_cast<const S*>(u), static_cast<const S*>(F), part,
                                             g.nblocks, res, flag);
     return cudaGetLastError() == cudaSuccess ? PB_OK : PB_ECUDA;
 }

@@ -120,7 +120,7 @@ public:
 
     void ptl_finalize(Ctx& c, const void* u, const void* F) override {
         KScope ks(c.prof, c.stream, K_PTL_FINAL, (double)c.grid.nblocks * sizeof(ArgMax));
-        ptl_finalize_kernel<P><<<1, 256, 0, c.stream>>>(c.grid, static_cast<const S*>(u), static_cast<const S*>(F),
+        ptl_finalize_kernel<P><<<1, kFinalizeThreads, 0, c.stream>>>(c.grid, static_cast<const S*>(u), static_cast<const S*>(F),
                                                         static_cast<const ArgMax*>(c.partials), c.grid.nblocks,
                                                         c.d_ptl, c.d_flag);
         PB_CUDA_TRY(cudaGetLastError());
@@ -134,7 +134,7 @@ public:
                                                              static_cast<const S*>(F), static_cast<ArgMax*>(c.partials));
             PB_CUDA_TRY(cudaGetLastError());
         }
-        ptl_full_finalize_kernel<<<1, 256, 0, c.stream>>>(static_cast<const ArgMax*>(c.partials), blocks, c.d_ptl);
+        ptl_full_finalize_kernel<<<1, kFinalizeThreads, 0, c.stream>>>(static_cast<const ArgMax*>(c.partials), blocks, c.d_ptl);
         PB_CUDA_TRY(cudaGetLastError());
     }
 
