@@ -86,7 +86,8 @@ void free_ctx(Ctx& c) {
     free_shadow(c.shadow);
     c.shadow = nullptr;
     void* ptrs[] = {c.coef, c.coef_be, c.coef64, c.adiag, c.y0, c.buf[0], c.buf[1], c.buf[2], c.r, c.p[0],
-                    c.p[1], c.q, c.dinv, c.partials, c.counter, c.d_ptl, c.d_pcg, c.d_scalar, c.d_flag, c.d_err};
+                    c.p[1], c.q, c.dinv, c.partials, c.counter, c.d_pcg, c.d_scalar, c.d_flag, c.d_err,
+                    c.spec};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c.s64) cudaFree(c.s64);
@@ -96,6 +97,13 @@ void free_ctx(Ctx& c) {
     if (c.h_pcg) cudaFreeHost(c.h_pcg);
     if (c.h_scalar) cudaFreeHost(c.h_scalar);
     if (c.h_err) cudaFreeHost(c.h_err);
+    if (c.ev_ptl) cudaEventDestroy(c.ev_ptl);
+}
+
+// Second state buffer for speculated cycles, and the event the host waits on for a PTL result.
+void* ensure_spec(Ctx& c) {
+    if (!c.spec) c.spec = dmalloc((size_t)c.n * c.elem);
+    return c.spec;
 }
 
 void ensure_pcg_buffers(Ctx& c) {
@@ -222,8 +230,7 @@ PtlResult run_ptl(Ctx& c, Ops* ops, const void* u, bool full = false) {
     ops->y0_pass(c, u, c.y0, true, nullptr, 0.0);
     ops->ptl_finalize(c, u, c.y0);
     if (full) ops->ptl_full(c, u, c.y0);
-    PB_CUDA_TRY(cudaMemcpyAsync(c.h_ptl, c.d_ptl, sizeof(PtlResult), cudaMemcpyDeviceToHost, c.stream));
-    sync(c);
+    sync(c);                 // the finalisers write the result straight into mapped host memory
     return *c.h_ptl;
 }
 
@@ -322,7 +329,10 @@ int parabolic_setup(const pb_grid* g, const pb_operator* op, int32_t precision, 
             c.partial_cap = std::max(c.grid.nblocks, 3 * reduce_blocks(c)) + 32;
             c.partials = dmalloc((size_t)c.partial_cap * 32);
             c.counter = static_cast<unsigned int*>(dmalloc(sizeof(unsigned int)));
-            c.d_ptl = static_cast<PtlResult*>(dmalloc(sizeof(PtlResult)));
+            // the PTL result lives in mapped pinned host memory: the finalising kernels write it
+            // there, so reading it back needs no copy in the stream
+            PB_CUDA_TRY(cudaHostAlloc(&c.h_ptl, sizeof(PtlResult), cudaHostAllocMapped));
+            PB_CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&c.d_ptl), c.h_ptl, 0));
             c.d_pcg = static_cast<PcgScalars*>(dmalloc(sizeof(PcgScalars)));
             c.d_scalar = static_cast<double*>(dmalloc(sizeof(double)));
             c.d_flag = static_cast<int*>(dmalloc(sizeof(int)));
@@ -335,7 +345,7 @@ int parabolic_setup(const pb_grid* g, const pb_operator* op, int32_t precision, 
                 const char* e = getenv("PB_DISABLE_TMA");
                 c.use_tma = !(e && e[0] == '1') && c.geometry == PB_SPHERICAL;
             }
-            PB_CUDA_TRY(cudaMallocHost(&c.h_ptl, sizeof(PtlResult)));
+            PB_CUDA_TRY(cudaEventCreateWithFlags(&c.ev_ptl, cudaEventDisableTiming));
             PB_CUDA_TRY(cudaMallocHost(&c.h_pcg, sizeof(PcgScalars)));
             PB_CUDA_TRY(cudaMallocHost(&c.h_scalar, sizeof(double)));
             PB_CUDA_TRY(cudaMemsetAsync(c.counter, 0, sizeof(unsigned int), c.stream));
@@ -457,6 +467,7 @@ int rkl2_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, pb_
     Ctx& c = h->c;
     stats_begin(st, c);
     int cycle = 0;
+    void* cur = u;                  // holds the state of the last completed cycle
     const int rc = guarded(&c, [&] {
         const pb_advance_opts o = resolve(opts);
         if (!u) throw Error{PB_EINVAL, "null state pointer"};
@@ -464,12 +475,38 @@ int rkl2_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, pb_
         Ops* ops = ops_of(c);
         const bool forced = o.n_forced > 0;
         const bool want_full = o.ptl_mode == PB_PTL_FULL || (st && st->dt_full_cycle);
+        const double floor_dt = o.ptl_floor * c.dt_e;
         double t_rem = dt;
         Sts co;
+        // the stages of one cycle of length dt_c (y0 = F(in) in c.y0) from `in` into `out`, in
+        // increment form d_k = u_k - u_0 (see EpiStage): stages 1 and 2 fused (d1 = mut_1 dt y0 in
+        // buf[0]), d_k in buf[(k-1) % 3], the last stage writes u_0 + d_s into out.  in == out is
+        // allowed: the last stage reads u_0 at its own point only.
+        auto stages = [&](double dt_c, const void* in, void* out) {
+            const double a1 = co.mut[1] * dt_c;
+            const StageCoef k2{co.mu[2], co.nu[2], co.mut[2] * dt_c, (co.mut[2] + co.gt[2]) * dt_c};
+            if (co.s == 2) ops->stage2(c, c.y0, nullptr, in, out, a1, k2);
+            else ops->stage2(c, c.y0, c.buf[0], nullptr, c.buf[1], a1, k2);
+            for (int k = 3; k <= co.s; ++k) {
+                const bool last = k == co.s;
+                ops->stage(c, c.buf[(k - 2) % 3], c.buf[(k - 3) % 3], last ? in : nullptr, c.y0,
+                           last ? out : c.buf[(k - 1) % 3],
+                           StageCoef{co.mu[k], co.nu[k], co.mut[k] * dt_c, (co.mut[k] + co.gt[k]) * dt_c});
+            }
+        };
+        auto take = [&](const PtlResult& r, double& dtp, double& dfull, long long& kk) {
+            if (r.nonfinite) throw Error{PB_ENONFINITE, "non-finite F in the PTL pass"};
+            dtp = o.ptl_mode == PB_PTL_FULL ? r.dt_full : r.dt_ptl;
+            dfull = r.dt_full;
+            kk = r.k;
+            if (st) { st->last_dt_ptl = dtp; st->fmax = r.fmax; st->k_index = r.k; }
+        };
+        bool have_r = false;        // a PTL result of `cur` is at hand (y0 = F(cur) in c.y0)
+        PtlResult pend{};
         for (cycle = 0;; ++cycle) {
             double dt_c, dtp = std::numeric_limits<double>::quiet_NaN(), dfull = dtp;
             long long kk = -1;
-            bool y0_done = false;
+            bool y0_done = false, floored = false;
             if (forced) {
                 if (cycle >= o.n_forced) break;
                 dt_c = o.dt_cycles[cycle];
@@ -478,42 +515,63 @@ int rkl2_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, pb_
                 if (!(t_rem > 1e-12 * dt)) break;
                 if (cycle >= o.max_cycles) throw Error{PB_EMAXCYCLES, "PTL cycle count above max_cycles"};
                 if (o.use_ptl) {
-                    const PtlResult r = run_ptl(c, ops, u, want_full);
-                    if (r.nonfinite) throw Error{PB_ENONFINITE, "non-finite F in the PTL pass"};
-                    dtp = r.dt_ptl;
-                    dfull = r.dt_full;
-                    kk = r.k;
-                    if (o.ptl_mode == PB_PTL_FULL) dtp = r.dt_full;
-                    if (st) { st->last_dt_ptl = dtp; st->fmax = r.fmax; st->k_index = r.k; }
-                    dt_c = cycle_length(t_rem, dtp, o.ptl_floor * c.dt_e);
+                    const PtlResult r = have_r ? pend : run_ptl(c, ops, cur, want_full);
+                    have_r = false;
+                    take(r, dtp, dfull, kk);
+                    dt_c = cycle_length(t_rem, dtp, floor_dt);
+                    floored = !(dtp > floor_dt);
                     y0_done = true;
                 } else {
                     dt_c = t_rem;
                 }
             }
             make_sts(o.scheme, dt_c / c.dt_e, co);
-            // stage loop in increment form d_k = u_k - u_0 (see EpiStage): y0 = F(u0) (from the
-            // PTL pass, or computed here), stages 1 and 2 fused (d1 = mut_1 dt y0 in buf[0]),
-            // d_k in buf[(k-1) % 3], and the last stage writes u_0 + d_s into u
-            const double a1 = co.mut[1] * dt_c;
-            if (!y0_done) ops->apply(c, u, c.y0);
-            const StageCoef k2{co.mu[2], co.nu[2], co.mut[2] * dt_c, (co.mut[2] + co.gt[2]) * dt_c};
-            if (co.s == 2) ops->stage2(c, c.y0, nullptr, u, u, a1, k2);
-            else ops->stage2(c, c.y0, c.buf[0], nullptr, c.buf[1], a1, k2);
-            for (int k = 3; k <= co.s; ++k) {
-                const void* dkm1 = c.buf[(k - 2) % 3];
-                const void* dkm2 = c.buf[(k - 3) % 3];
-                const bool last = k == co.s;
-                void* out = last ? u : c.buf[(k - 1) % 3];
-                ops->stage(c, dkm1, dkm2, last ? u : nullptr, c.y0, out,
-                           StageCoef{co.mu[k], co.nu[k], co.mut[k] * dt_c, (co.mut[k] + co.gt[k]) * dt_c});
-            }
+            if (!y0_done) ops->apply(c, cur, c.y0);
+            stages(dt_c, cur, cur);
             if (st) st->total_stages += co.s;
             stats_cycle(st, dt_c, co.s, dtp, kk, dfull);
             t_rem -= dt_c;
+            // At the floor the next cycle most likely has the same length (t_rem / n, then
+            // (t_rem - t_rem/n) / (n - 1)): its PTL pass and, speculatively, its stages are queued
+            // into the other buffer before the host reads that PTL result, so the GPU does not
+            // wait for the host.  The speculation is kept when the decided length matches.
+            while (floored && t_rem > 1e-12 * dt && cycle + 1 < o.max_cycles) {
+                ops->y0_pass(c, cur, c.y0, true, nullptr, 0.0);
+                ops->ptl_finalize(c, cur, c.y0);
+                if (want_full) ops->ptl_full(c, cur, c.y0);
+                PB_CUDA_TRY(cudaEventRecord(c.ev_ptl, c.stream));
+                void* nxt = cur == u ? ensure_spec(c) : u;
+                stages(dt_c, cur, nxt);
+                PB_CUDA_TRY(cudaEventSynchronize(c.ev_ptl));
+                const PtlResult r = *c.h_ptl;
+                double dtp2, dfull2;
+                long long kk2;
+                take(r, dtp2, dfull2, kk2);
+                const double dt_c2 = cycle_length(t_rem, dtp2, floor_dt);
+                if (!(std::fabs(dt_c2 - dt_c) <= 1e-12 * dt_c)) {   // not the speculated cycle
+                    pend = r;
+                    have_r = true;
+                    break;
+                }
+                ++cycle;
+                cur = nxt;
+                if (st) st->total_stages += co.s;
+                stats_cycle(st, dt_c, co.s, dtp2, kk2, dfull2);
+                t_rem -= dt_c;
+                floored = !(dtp2 > floor_dt);
+            }
+        }
+        if (cur != u) {
+            PB_CUDA_TRY(cudaMemcpyAsync(u, cur, (size_t)c.n * c.elem, cudaMemcpyDeviceToDevice, c.stream));
+            cur = u;
         }
         sync(c);
     });
+    if (rc != PB_OK && cur != u) {
+        // the last completed cycle lives in the speculation buffer: hand it back
+        cudaMemcpyAsync(u, cur, (size_t)c.n * c.elem, cudaMemcpyDeviceToDevice, c.stream);
+        cudaStreamSynchronize(c.stream);
+    }
     if (rc != PB_OK && st) st->status_cycle = cycle;
     return rc;
 }

@@ -143,6 +143,8 @@ struct Ctx {
     double* geo[16] = {};          // device copies of the face / point coordinate arrays
     Prof prof;
     struct Ctx* shadow = nullptr;  // float32 shadow for mixed-precision BE (float64 contexts)
+    void* spec = nullptr;          // second state buffer of speculated floor cycles [n]
+    cudaEvent_t ev_ptl = nullptr;  // recorded after a PTL result's copy to the host
     std::string err;
     int sm_count = 0;
 };
