@@ -608,7 +608,8 @@ def fig1_probe(pb, torch, n_phi=256, ratio=500.0):
 
 def precision_stress_probe(pb, torch, bf16_cap=5000):
     """The jump128 workload (128 x 256 x 512 shell, temperature jump at r = 1.02 over three radial
-    cells, 5 % noise; RKL2 + PTL over dt = 1e5 dt_E) in float64, float32 and bfloat16 storage:
+    cells, 5 % noise; RKL2 + PTL over dt = 1e5 dt_E) in float64, float32, bfloat16 storage and
+    float64 storage with the float32 stencil (fp64s):
     each precision's own PTL schedule (cycles, stages, time; bfloat16 capped at bf16_cap cycles),
     and its error against the float64 oracle's sampled final state when it replays the oracle's
     schedule (tests/golden/jump128_rkl2_ptl.txt, written by the oracle-only script beside it)."""
@@ -629,7 +630,8 @@ def precision_stress_probe(pb, torch, bf16_cap=5000):
     idx = torch.from_numpy(gold["idx"]).to("cuda")
     out = {"what": "jump128: 128x256x512 shell, T jump at r = 1.02 (3 cells), RKL2 + PTL over 1e5 dt_E",
            "oracle": {"cycles": len(gold["dt_c"]), "stages": int(sum(gold["s"]))}}
-    for prec, dtype in (("fp64", torch.float64), ("fp32", torch.float32), ("bf16", torch.bfloat16)):
+    for prec, dtype in (("fp64", torch.float64), ("fp32", torch.float32), ("bf16", torch.bfloat16),
+                        ("fp64s", torch.float64)):
         ctx = pb.parabolic_setup(g.r_face, g.t_face, g.n_phi, "tc", fields, prec)
         dt = wl["ratio"] * pb.parabolic_dt_explicit(ctx)
         rec = {}

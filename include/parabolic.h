@@ -61,7 +61,12 @@ extern "C" {
 #define PB_ETIMEOUT      7  /* a bounded device-side wait ran out                           */
 #define PB_ENOTSUP       8  /* combination not supported by this build                      */
 
-typedef enum { PB_FP64 = 0, PB_FP32 = 1, PB_BF16_STORE = 2 } pb_precision;
+/* PB_FP64: float64 states, records and arithmetic.  PB_FP32: float32 throughout (reductions and
+ * coefficients in float64).  PB_BF16_STORE: bfloat16 states, float32 records and arithmetic.
+ * PB_FP64_STORE: float64 states and stage recurrence, float32 records and stencil arithmetic --
+ * the storage rounding that accumulates over the stages of a long cycle is that of float64,
+ * while the stencil runs at float32 rates (STS only; BE + PCG needs PB_FP64 or PB_FP32). */
+typedef enum { PB_FP64 = 0, PB_FP32 = 1, PB_BF16_STORE = 2, PB_FP64_STORE = 3 } pb_precision;
 typedef enum { PB_TC_ANISO = 0, PB_VISC_ISO = 1 } pb_op_kind;
 typedef enum { PB_RKL2 = 0, PB_RKG2 = 1 } pb_scheme;
 /* Where the PTL condition is evaluated: at argmax |F| only (Eq. 5) or over every pair of face
@@ -162,8 +167,8 @@ PB_API const char* pb_last_error(const pb_ctx* ctx);
 /* Builds a context: validates the grid, allocates its device workspace (owned by the context),
  * computes the frozen operator coefficients in float64 on the device (lagged kappa, Sec. 2) and
  * stores them in the context precision, and reduces dt_E.  precision: PB_FP64, PB_FP32 (float
- * state and arithmetic; PTL and PCG reductions in float64) or PB_BF16_STORE (bfloat16 state,
- * float coefficients and arithmetic).  cuda_stream is a cudaStream_t (NULL = legacy default). */
+ * state and arithmetic; PTL and PCG reductions in float64), PB_BF16_STORE (bfloat16 state,
+ * float coefficients and arithmetic) or PB_FP64_STORE (see pb_precision).  cuda_stream is a cudaStream_t (NULL = legacy default). */
 PB_API int parabolic_setup(const pb_grid* grid, const pb_operator* op, int32_t precision,
                     void* cuda_stream, pb_ctx** out);
 

@@ -21,7 +21,8 @@ PB_FP64, PB_FP32, PB_BF16_STORE = 0, 1, 2
 PB_TC_ANISO, PB_VISC_ISO = 0, 1
 PB_RKL2, PB_RKG2 = 0, 1
 
-PRECISIONS = {"fp64": PB_FP64, "fp32": PB_FP32, "bf16": PB_BF16_STORE}
+PB_FP64_STORE = 3
+PRECISIONS = {"fp64": PB_FP64, "fp32": PB_FP32, "bf16": PB_BF16_STORE, "fp64s": PB_FP64_STORE}
 SCHEMES = {"rkl2": PB_RKL2, "rkg2": PB_RKG2}
 PB_PTL_FMAX, PB_PTL_FULL = 0, 1
 PB_SPHERICAL, PB_CARTESIAN_PERIODIC = 0, 1
@@ -197,7 +198,8 @@ class Context:
     @property
     def dtype(self):
         torch = _torch()
-        return {PB_FP64: torch.float64, PB_FP32: torch.float32, PB_BF16_STORE: torch.bfloat16}[self.precision]
+        return {PB_FP64: torch.float64, PB_FP32: torch.float32, PB_BF16_STORE: torch.bfloat16,
+                PB_FP64_STORE: torch.float64}[self.precision]
 
     def close(self):
         if self.handle:

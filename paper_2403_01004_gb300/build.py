@@ -14,7 +14,7 @@ LIBDIR = os.path.join(PKG, "lib")
 OBJDIR = os.path.join(PKG, "lib", "obj")
 LIB = os.path.join(LIBDIR, "libparabolic.so")
 
-SOURCES = ["api.cu", "setup.cu", "tma_host.cu", "noalloc.cu", "batch.cu", "convnet.cu", "mixed.cu", "ops_f64.cu", "ops_f32.cu", "ops_b16.cu"]
+SOURCES = ["api.cu", "setup.cu", "tma_host.cu", "noalloc.cu", "batch.cu", "convnet.cu", "mixed.cu", "ops_f64.cu", "ops_f32.cu", "ops_b16.cu", "ops_f64s.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

@@ -23,6 +23,7 @@ Ops* ops_of(const Ctx& c) {
     switch (c.prec) {
         case PB_FP64: return ops_f64();
         case PB_FP32: return ops_f32();
+        case PB_FP64_STORE: return ops_f64s();
         default: return ops_b16();
     }
 }
@@ -303,7 +304,8 @@ int parabolic_setup(const pb_grid* g, const pb_operator* op, int32_t precision, 
                 if (!(g->t_face[j + 1] > g->t_face[j])) throw Error{PB_EINVAL, "t_face must increase"};
         }
         if ((long long)g->n_r * g->n_theta * g->n_phi > (1LL << 40)) throw Error{PB_EINVAL, "grid too large"};
-        if (precision != PB_FP64 && precision != PB_FP32 && precision != PB_BF16_STORE) throw Error{PB_EINVAL, "bad precision"};
+        if (precision != PB_FP64 && precision != PB_FP32 && precision != PB_BF16_STORE && precision != PB_FP64_STORE)
+            throw Error{PB_EINVAL, "bad precision"};
         if (op->kind != PB_TC_ANISO && op->kind != PB_VISC_ISO) throw Error{PB_EINVAL, "unknown operator kind"};
         check_operator(op->kind, op);
         int dev = 0;
@@ -313,7 +315,7 @@ int parabolic_setup(const pb_grid* g, const pb_operator* op, int32_t precision, 
         try {
             c.kind = op->kind;
             c.prec = precision;
-            c.elem = precision == PB_FP64 ? 8 : precision == PB_FP32 ? 4 : 2;
+            c.elem = (precision == PB_FP64 || precision == PB_FP64_STORE) ? 8 : precision == PB_FP32 ? 4 : 2;
             c.stream = static_cast<cudaStream_t>(stream);
             c.nr = g->n_r; c.nt = g->n_theta; c.np = g->n_phi;
             c.geometry = g->geometry;
@@ -586,7 +588,7 @@ int be_pcg_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, c
         if (!u) throw Error{PB_EINVAL, "null state pointer"};
         if (!(dt >= 0.0) || std::isinf(dt)) throw Error{PB_EINVAL, "dt must be finite and >= 0"};
         Ops* ops = ops_of(c);
-        if (!ops->supports_pcg()) throw Error{PB_ENOTSUP, "BE + PCG needs PB_FP64 or PB_FP32 storage"};
+        if (!ops->supports_pcg()) throw Error{PB_ENOTSUP, "BE + PCG needs PB_FP64 or PB_FP32 contexts"};
         ensure_pcg_buffers(c);
         const bool forced = o.n_forced > 0;
         const bool want_full = o.ptl_mode == PB_PTL_FULL || (st && st->dt_full_cycle);

@@ -18,9 +18,14 @@ namespace pb {
 // S: state storage, C: coefficient storage, A: stencil / stage arithmetic.
 // CG: operands may have been written earlier in the same launch (the batched persistent kernel),
 // so they are read through L2 (ld.global.cg) instead of the non-coherent read-only path.
-struct PolF64 { using S = double; using C = double; using A = double; static constexpr int id = PB_FP64; static constexpr bool CG = false; };
-struct PolF32 { using S = float; using C = float; using A = float; static constexpr int id = PB_FP32; static constexpr bool CG = false; };
-struct PolB16 { using S = __nv_bfloat16; using C = float; using A = float; static constexpr int id = PB_BF16_STORE; static constexpr bool CG = false; };
+// S: storage of states and stage values; C: coefficient records; A: stencil arithmetic;
+// E: the stage recurrence (the update of the stored stage values from A-precision F).
+struct PolF64 { using S = double; using C = double; using A = double; using E = double; static constexpr int id = PB_FP64; static constexpr bool CG = false; };
+struct PolF32 { using S = float; using C = float; using A = float; using E = float; static constexpr int id = PB_FP32; static constexpr bool CG = false; };
+struct PolB16 { using S = __nv_bfloat16; using C = float; using A = float; using E = float; static constexpr int id = PB_BF16_STORE; static constexpr bool CG = false; };
+// float64 storage and recurrence, float32 records and stencil (GB300: float64 arithmetic is
+// scarce, bandwidth is not; the stage recurrence is where storage rounding accumulates)
+struct PolF64S { using S = double; using C = float; using A = float; using E = double; static constexpr int id = PB_FP64_STORE; static constexpr bool CG = false; };
 struct PolF32CG : PolF32 { static constexpr bool CG = true; };
 
 template <typename T> __host__ __device__ __forceinline__ float to_f(T v);

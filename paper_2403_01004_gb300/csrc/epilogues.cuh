@@ -62,7 +62,8 @@ struct EpiF {
     __device__ void init() { bv = A(-1); bi = LLONG_MAX; bad = 0; }
     __device__ bool skip() const { return false; }
     __device__ Pre prefetch(long long) const { return {}; }
-    __device__ void apply_c(long long idx, A Au, A w, A center, A, A, A) { apply(idx, Au, w, center, Pre{}); }
+    using E = typename P::E;
+    __device__ void apply_c(long long idx, A Au, A w, E center, E, E, E) { apply(idx, Au, w, (A)center, Pre{}); }
     __device__ void apply(long long idx, A Au, A w, A center, const Pre&) {
         const A f = w * Au;
         const S fs = cvt<S>(f);
@@ -96,25 +97,34 @@ template <class P, bool KM2, bool LAST>
 struct EpiStage {
     using A = typename P::A;
     using S = typename P::S;
-    struct Pre { A dkm2, y0, u0; };
+    using E = typename P::E;
+    // E wider than A: the register-path kernels hand over d_{k-1} in A, so its stored value is
+    // reloaded (the TMA kernel hands it over exactly)
+    static constexpr bool kExact = sizeof(E) > sizeof(A);
+    struct Pre { E dkm2, y0, u0, dkm1; };
     const S* dkm2;
     const S* y0;
     const S* u0;
     S* out;
-    A mu, nu, mdt, ydt;
+    E mu, nu, mdt, ydt;
+    const S* dkm1;
     // point operands of the TMA kernel, in this order: y0, d_{k-2} (KM2), u0 (LAST)
     static constexpr int NC = 1 + (KM2 ? 1 : 0) + (LAST ? 1 : 0);
-    __device__ void apply_c(long long idx, A Au, A w, A dkm1, A c0, A c1, A c2) {
-        apply(idx, Au, w, dkm1, Pre{KM2 ? c1 : A(0), c0, LAST ? (KM2 ? c2 : c1) : A(0)});
+    __device__ void apply_c(long long idx, A Au, A w, E d1, E c0, E c1, E c2) {
+        update(idx, Au, w, d1, KM2 ? c1 : E(0), c0, LAST ? (KM2 ? c2 : c1) : E(0));
     }
     __device__ void init() {}
     __device__ bool skip() const { return false; }
     __device__ Pre prefetch(long long idx) const {
-        return Pre{KM2 ? cvt<A>(ldx<P>(dkm2 + idx)) : A(0), cvt<A>(ldx<P>(y0 + idx)), LAST ? cvt<A>(u0[idx]) : A(0)};
+        return Pre{KM2 ? cvt<E>(ldx<P>(dkm2 + idx)) : E(0), cvt<E>(ldx<P>(y0 + idx)), LAST ? cvt<E>(u0[idx]) : E(0),
+                   kExact ? cvt<E>(ldx<P>(dkm1 + idx)) : E(0)};
     }
-    __device__ void apply(long long idx, A Au, A w, A dkm1, const Pre& p) {
-        const A d = mu * dkm1 + nu * p.dkm2 + mdt * (w * Au) + ydt * p.y0;
-        out[idx] = cvt<S>(LAST ? p.u0 + d : d);
+    __device__ void apply(long long idx, A Au, A w, A d1, const Pre& p) {
+        update(idx, Au, w, kExact ? p.dkm1 : (E)d1, p.dkm2, p.y0, p.u0);
+    }
+    __device__ void update(long long idx, A Au, A w, E d1, E d2, E y, E u) {
+        const E d = mu * d1 + nu * d2 + mdt * (E)(w * Au) + ydt * y;
+        out[idx] = cvt<S>(LAST ? u + d : d);
     }
     __device__ void finish() {}
 };
@@ -128,20 +138,26 @@ template <class P, bool LAST>
 struct EpiStage2 {
     using A = typename P::A;
     using S = typename P::S;
-    struct Pre { A u0; };
+    using E = typename P::E;
+    static constexpr bool kExact = sizeof(E) > sizeof(A);
+    struct Pre { E u0, y; };
     const S* u0;
     S* d1;
     S* out;
-    A a, cy, cf;       // a = mut_1 dt, cy = mu_2 a + ydt, cf = mdt a
+    E a, cy, cf;       // a = mut_1 dt, cy = mu_2 a + ydt, cf = mdt a
+    const S* y0;       // the marched field, reloaded exactly when E is wider than A
     static constexpr int NC = LAST ? 1 : 0;
     __device__ void init() {}
     __device__ bool skip() const { return false; }
-    __device__ Pre prefetch(long long idx) const { return Pre{LAST ? cvt<A>(u0[idx]) : A(0)}; }
-    __device__ void apply_c(long long idx, A Au, A w, A y, A c0, A, A) { apply(idx, Au, w, y, Pre{c0}); }
-    __device__ void apply(long long idx, A Au, A w, A y, const Pre& p) {
-        const A d2 = cy * y + cf * (w * Au);
+    __device__ Pre prefetch(long long idx) const {
+        return Pre{LAST ? cvt<E>(u0[idx]) : E(0), kExact ? cvt<E>(ldx<P>(y0 + idx)) : E(0)};
+    }
+    __device__ void apply_c(long long idx, A Au, A w, E y, E c0, E, E) { update(idx, Au, w, y, c0); }
+    __device__ void apply(long long idx, A Au, A w, A y, const Pre& p) { update(idx, Au, w, kExact ? p.y : (E)y, p.u0); }
+    __device__ void update(long long idx, A Au, A w, E y, E u) {
+        const E d2 = cy * y + cf * (E)(w * Au);
         if (LAST) {
-            out[idx] = cvt<S>(p.u0 + d2);
+            out[idx] = cvt<S>(u + d2);
         } else {
             d1[idx] = cvt<S>(a * y);
             out[idx] = cvt<S>(d2);
@@ -237,7 +253,8 @@ struct EpiPcgSpmv {
     }
     __device__ bool skip() const { return done != 0; }
     __device__ Pre prefetch(long long) const { return {}; }
-    __device__ void apply_c(long long idx, A Au, A m, A pv, A, A, A) { apply(idx, Au, m, pv, Pre{}); }
+    using E = typename P::E;
+    __device__ void apply_c(long long idx, A Au, A m, E pv, E, E, E) { apply(idx, Au, m, (A)pv, Pre{}); }
     __device__ void apply(long long idx, A Au, A m, A pv, const Pre&) {
         const S ps = cvt<S>(pv);
         const S qs = cvt<S>(m * pv - dt * Au);

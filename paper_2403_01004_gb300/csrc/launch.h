@@ -41,6 +41,7 @@ public:
 Ops* ops_f64();
 Ops* ops_f32();
 Ops* ops_b16();
+Ops* ops_f64s();   // PolF64S: float64 storage and recurrence, float32 stencil
 
 // set-up kernels (float64), see setup.cu.  setup_tc / setup_visc leave diag(A) in c.s64.
 void setup_geometry(Ctx& c, const pb_grid& g);

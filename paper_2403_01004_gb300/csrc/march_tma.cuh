@@ -209,12 +209,14 @@ tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* 
         if (!wait(q + 1)) { bail(issued, q + 1); return; }
         const A w = corner(kb ^ 1, q, tx + 1, ty + 1);
         if (xci >= 0) corner(kb ^ 1, q, xci, xcj);
-        const A center = U(q, ty + 1, tx + L::HX);
-        auto cen = [&](int a) -> A {
-            return a < Epi::NC ? cvt<A>(reinterpret_cast<const S*>(slot(q) + L::E_OFF + a * align128(L::E_BYTES))[ty * TX + tx])
-                               : A(0);
+        // the centre and the point operands go to the epilogue at the stage-recurrence precision E
+        using R = typename P::E;
+        const R center = cvt<R>(reinterpret_cast<const S*>(slot(q) + L::FIELD_OFF)[(ty + 1) * L::BXW + tx + L::HX]);
+        auto cen = [&](int a) -> R {
+            return a < Epi::NC ? cvt<R>(reinterpret_cast<const S*>(slot(q) + L::E_OFF + a * align128(L::E_BYTES))[ty * TX + tx])
+                               : R(0);
         };
-        const A c0 = cen(0), c1 = cen(1), c2 = cen(2);
+        const R c0 = cen(0), c1 = cen(1), c2 = cen(2);
         __syncthreads();
         // slot q is no longer read: refill it with plane k0-1+q+kSlots
         if (tid == 0 && issued < nplanes) issue(issued);

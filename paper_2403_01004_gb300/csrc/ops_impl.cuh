@@ -16,6 +16,7 @@ class OpsImpl : public Ops {
     using S = typename P::S;
     using C = typename P::C;
     using A = typename P::A;
+    using E = typename P::E;
 
     template <class Load, class Epi>
     static void march(Ctx& c, const void* coef, const Load& ld, const Epi& ep) {
@@ -85,7 +86,7 @@ class OpsImpl : public Ops {
     }
 
 public:
-    bool supports_pcg() const override { return P::id != PB_BF16_STORE; }
+    bool supports_pcg() const override { return P::id == PB_FP64 || P::id == PB_FP32; }
 
     static double nb(const Ctx& c, double s_words, double c_words) {
         return (double)c.n * (s_words * sizeof(S) + c_words * sizeof(C));
@@ -148,8 +149,8 @@ public:
     template <bool LAST>
     void stage2_t(Ctx& c, const void* y0, void* d1, const void* u0, void* out, double a1, const StageCoef& k) {
         KScope ks(c.prof, c.stream, K_STAGE, nb(c, 3, 4));
-        EpiStage2<P, LAST> ep{static_cast<const S*>(u0), static_cast<S*>(d1), static_cast<S*>(out), (A)a1,
-                              (A)(k.mu * a1 + k.ydt), (A)(k.mdt * a1)};
+        EpiStage2<P, LAST> ep{static_cast<const S*>(u0), static_cast<S*>(d1), static_cast<S*>(out), (E)a1,
+                              (E)(k.mu * a1 + k.ydt), (E)(k.mdt * a1), static_cast<const S*>(y0)};
         const void* cen[1] = {u0};
         march_state(c, y0, cen, ep);
     }
@@ -163,7 +164,8 @@ public:
     void stage_t(Ctx& c, const void* dkm1, const void* dkm2, const void* u0, const void* y0, void* out,
                  const StageCoef& k) {
         EpiStage<P, KM2, LAST> ep{static_cast<const S*>(dkm2), static_cast<const S*>(y0), static_cast<const S*>(u0),
-                                  static_cast<S*>(out), (A)k.mu, (A)k.nu, (A)k.mdt, (A)k.ydt};
+                                  static_cast<S*>(out), (E)k.mu, (E)k.nu, (E)k.mdt, (E)k.ydt,
+                                  static_cast<const S*>(dkm1)};
         KScope ks(c.prof, c.stream, K_STAGE, nb(c, 3 + (KM2 ? 1 : 0) + (LAST ? 1 : 0), 4));
         const void* cen[3];
         int n = 0;

@@ -206,11 +206,13 @@ def test_sts_ptl_fp64_matches_oracle_schedule_and_state(kind, scheme):
     assert (M * ug).sum() == pytest.approx((M * u_in).sum(), rel=1e-13)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp64s"])
 @pytest.mark.parametrize("kind", ["tc", "visc"])
 def test_sts_reduced_precision_forced_schedule(kind, prec):
     """The schedule is taken from the oracle's FP64 PTL run and replayed on both sides, so the
-    comparison isolates the arithmetic precision from the (discontinuous) cycle decisions."""
+    comparison isolates the arithmetic precision from the (discontinuous) cycle decisions.
+    fp64s (float64 storage, float32 stencil) is held to the float32 tolerance: its stencil
+    arithmetic is float32."""
     if kind == "visc" and prec == "bf16":
         pytest.skip("bf16 storage targets the conduction workload")
     shape = (32, 32, 64) if kind == "tc" else (24, 20, 16)
@@ -218,7 +220,8 @@ def test_sts_reduced_precision_forced_schedule(kind, prec):
     _, log = sts_advance(op, u, 100.0 * op.dt_explicit(), "rkl2", use_ptl=True)
     st, log2, ug, uo, _, _ = _sts_compare(kind, shape, "rkl2", prec, forced=log.dt_c)
     assert st["work_cycle"] == log2.s
-    assert rel_l2(ug, uo) <= TOL[prec], rel_l2(ug, uo)
+    tol = TOL["fp32" if prec == "fp64s" else prec]
+    assert rel_l2(ug, uo) <= tol, rel_l2(ug, uo)
 
 
 def test_sts_no_ptl_single_cycle_fp64():
@@ -268,6 +271,15 @@ def test_be_fp32_fixed_iterations():
     assert rel_l2(to_host(ud), res.x) <= TOL["fp32"], rel_l2(to_host(ud), res.x)
 
 
+def test_fp64_storage_refuses_pcg():
+    """Float64 storage with a float32 stencil cannot reach the PCG tolerances: BE is refused."""
+    import paper_2403_01004_gb300 as pb
+    g, inp, op, u = tc_problem(16, 12, 8)
+    ctx = gpu_ctx("tc", g, inp, "fp64s")
+    st = pb.be_pcg_advance(ctx, to_dev(u, ctx), 10.0 * op.dt_explicit(), raise_on_error=False)
+    assert st["status"] == pb.PB_ENOTSUP
+
+
 def test_errors_nonfinite_maxcycles_noconverge():
     import paper_2403_01004_gb300 as pb
     g, inp, op, u = tc_problem(16, 12, 8)
@@ -290,7 +302,7 @@ def test_errors_nonfinite_maxcycles_noconverge():
     np.testing.assert_array_equal(to_host(ud), u)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16", "fp64s"])
 def test_tma_and_fallback_kernels_agree(prec, monkeypatch):
     """The TMA pipeline (aligned rows) and the register-prefetch kernel compute the same stages."""
     import paper_2403_01004_gb300 as pb
@@ -303,7 +315,7 @@ def test_tma_and_fallback_kernels_agree(prec, monkeypatch):
         ud = to_dev(u, ctx)
         pb.rkl2_advance(ctx, ud, dt, use_ptl=True)
         outs.append(to_host(ud))
-    assert rel_l2(outs[0], outs[1]) <= {"fp64": 1e-14, "fp32": 1e-6, "bf16": 1e-2}[prec]
+    assert rel_l2(outs[0], outs[1]) <= {"fp64": 1e-14, "fp32": 1e-6, "bf16": 1e-2, "fp64s": 1e-6}[prec]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
