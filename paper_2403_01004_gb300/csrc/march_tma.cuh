@@ -19,6 +19,8 @@
 // never written by the threads.
 #pragma once
 
+#include <type_traits>
+
 #include "march.cuh"
 #include "tma.cuh"
 
@@ -34,8 +36,26 @@ __host__ __device__ constexpr int align128(int b) { return (b + 127) & ~127; }
 template <class P>
 struct PlainField {
     static constexpr int NF = 1;
+    static constexpr bool CENTER_RAW = true;     // the centre comes from the landed array
+    using FT = typename P::S;                    // element type the stencil reads
     __device__ void init() {}
-    __device__ void combine(unsigned char*, int, int, typename P::S*) const {}
+    __device__ void combine(unsigned char*, int, int, FT*) const {}
+};
+
+// One array stored wider than the stencil arithmetic (float64 storage, float32 stencil): the
+// halo box is converted once per plane instead of once per corner that reads it.
+template <class P>
+struct ConvField {
+    using A = typename P::A;
+    using S = typename P::S;
+    static constexpr int NF = 1;
+    static constexpr bool CENTER_RAW = true;
+    using FT = A;
+    __device__ void init() {}
+    __device__ void combine(unsigned char* base, int, int n, A* dst) const {
+        const S* f = reinterpret_cast<const S*>(base);
+        for (int e = threadIdx.x + TX * threadIdx.y; e < n; e += NTHREADS) dst[e] = cvt<A>(f[e]);
+    }
 };
 
 // The PCG search direction p = z + beta p_old with z = D^-1 r rounded to the state precision,
@@ -45,6 +65,8 @@ struct PcgField {
     using A = typename P::A;
     using S = typename P::S;
     static constexpr int NF = 3;
+    static constexpr bool CENTER_RAW = false;    // the centre is the assembled p
+    using FT = S;
     const PcgScalars* sc;
     A beta;
     int first;
@@ -64,23 +86,27 @@ struct PcgField {
     }
 };
 
-template <class P, int NC, int NF = 1>
+template <class P, int NC, class Field = PlainField<P>>
 struct TmaLayout {
     using S = typename P::S;
     using C = typename P::C;
     using A = typename P::A;
+    static constexpr int NF = Field::NF;
+    // a buffer of the assembled / converted field when the stencil does not read the landed array
+    static constexpr bool ASSEMBLED = NF > 1 || !std::is_same<typename Field::FT, S>::value;
     static constexpr int HX = HaloPad<S>::value;
     static constexpr int BXW = TX + 2 * HX;                              // halo box width (points)
     static constexpr int U_BYTES = (TY + 2) * BXW * (int)sizeof(S);
     static constexpr int U_PITCH = align128(U_BYTES);
+    static constexpr int F_BYTES = (TY + 2) * BXW * (int)sizeof(typename Field::FT);
     static constexpr int C_BYTES = (TY + 1) * (TX + 1) * 4 * (int)sizeof(C);
     static constexpr int E_BYTES = TY * TX * (int)sizeof(S);
     static constexpr int U_OFF = 0;
     static constexpr int C_OFF = NF * U_PITCH;
     static constexpr int E_OFF = C_OFF + align128(C_BYTES);
-    static constexpr int P_OFF = E_OFF + NC * align128(E_BYTES);         // assembled field (NF > 1)
-    static constexpr int FIELD_OFF = NF > 1 ? P_OFF : U_OFF;
-    static constexpr int SLOT = P_OFF + (NF > 1 ? U_PITCH : 0);
+    static constexpr int P_OFF = E_OFF + NC * align128(E_BYTES);         // assembled field
+    static constexpr int FIELD_OFF = ASSEMBLED ? P_OFF : U_OFF;
+    static constexpr int SLOT = P_OFF + (ASSEMBLED ? align128(F_BYTES) : 0);
     static constexpr int TX_BYTES = NF * U_BYTES + C_BYTES + NC * E_BYTES;   // bytes a slot's copies deliver
     static constexpr int CW = TX + 2;                                    // corner row pitch
     static constexpr int CORN_OFF = kSlots * SLOT;
@@ -95,7 +121,7 @@ tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* 
     using S = typename P::S;
     using C = typename P::C;
     using A = typename P::A;
-    using L = TmaLayout<P, Epi::NC, Field::NF>;
+    using L = TmaLayout<P, Epi::NC, Field>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // TMA destinations are kept 128-byte aligned (the launch adds 128 bytes of slack)
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -139,8 +165,9 @@ tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* 
         if (!mbar_wait(bars + (q % kSlots), (q / kSlots) & 1)) *abort_flag = 1;
         __syncthreads();
         if (*abort_flag != 0) return false;
-        if constexpr (Field::NF > 1) {
-            fld.combine(slot(q) + L::U_OFF, L::U_PITCH, (TY + 2) * L::BXW, reinterpret_cast<S*>(slot(q) + L::P_OFF));
+        if constexpr (L::ASSEMBLED) {
+            fld.combine(slot(q) + L::U_OFF, L::U_PITCH, (TY + 2) * L::BXW,
+                        reinterpret_cast<typename Field::FT*>(slot(q) + L::P_OFF));
             __syncthreads();
         }
         return true;
@@ -153,7 +180,7 @@ tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* 
         __syncthreads();
     };
     auto U = [&](int q, int yy, int xx) -> A {
-        return cvt<A>(reinterpret_cast<const S*>(slot(q) + L::FIELD_OFF)[yy * L::BXW + xx]);
+        return cvt<A>(reinterpret_cast<const typename Field::FT*>(slot(q) + L::FIELD_OFF)[yy * L::BXW + xx]);
     };
     // corner (ci, cj) of plane z = k0-1+q from field slots q (plane z) and q+1 (plane z+1)
     auto corner = [&](int cbuf, int q, int ci, int cj) -> A {
@@ -211,7 +238,9 @@ tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* 
         if (xci >= 0) corner(kb ^ 1, q, xci, xcj);
         // the centre and the point operands go to the epilogue at the stage-recurrence precision E
         using R = typename P::E;
-        const R center = cvt<R>(reinterpret_cast<const S*>(slot(q) + L::FIELD_OFF)[(ty + 1) * L::BXW + tx + L::HX]);
+        const R center = Field::CENTER_RAW
+                             ? cvt<R>(reinterpret_cast<const S*>(slot(q) + L::U_OFF)[(ty + 1) * L::BXW + tx + L::HX])
+                             : cvt<R>(reinterpret_cast<const typename Field::FT*>(slot(q) + L::FIELD_OFF)[(ty + 1) * L::BXW + tx + L::HX]);
         auto cen = [&](int a) -> R {
             return a < Epi::NC ? cvt<R>(reinterpret_cast<const S*>(slot(q) + L::E_OFF + a * align128(L::E_BYTES))[ty * TX + tx])
                                : R(0);

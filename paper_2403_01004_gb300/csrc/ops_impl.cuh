@@ -35,10 +35,13 @@ class OpsImpl : public Ops {
 
     // Conduction march on a plain state field through the TMA kernel when every array can be
     // described by a tensor map; otherwise the register-prefetch kernel.
+    // float64 storage with a float32 stencil converts the halo box once per plane
+    using StateField = typename std::conditional<(sizeof(S) > sizeof(A)), ConvField<P>, PlainField<P>>::type;
+
     template <class Epi>
     static void march_state(Ctx& c, const void* field, const void* const* cen, const Epi& ep) {
         if (c.kind == PB_TC_ANISO && c.use_tma) {
-            using L = TmaLayout<P, Epi::NC>;
+            using L = TmaLayout<P, Epi::NC, StateField>;
             const CompGrid& g = c.grid.c[0];
             TmaMaps maps;
             bool ok = tma_state_map(&maps.halo[0], field, sizeof(S), g.nr, g.nt, g.np, L::BXW, TY + 2) &&
@@ -49,10 +52,11 @@ class OpsImpl : public Ops {
                 static bool attr = false;
                 const int smem = L::TOTAL + 128;
                 if (!attr) {
-                    PB_CUDA_TRY(cudaFuncSetAttribute(tc_march_tma<P, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                    PB_CUDA_TRY(cudaFuncSetAttribute(tc_march_tma<P, Epi, StateField>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
                     attr = true;
                 }
-                tc_march_tma<P, Epi><<<c.grid.nblocks, dim3(TX, TY), smem, c.stream>>>(c.grid, maps, ep, c.d_err);
+                tc_march_tma<P, Epi, StateField><<<c.grid.nblocks, dim3(TX, TY), smem, c.stream>>>(c.grid, maps, ep, c.d_err);
                 PB_CUDA_TRY(cudaGetLastError());
                 return;
             }
@@ -65,7 +69,7 @@ class OpsImpl : public Ops {
     static bool pcg_spmv_tma(Ctx& c, const S* pold, const EpiPcgSpmv<P>& ep) {
         if (c.kind != PB_TC_ANISO || !c.use_tma) return false;
         using Fld = PcgField<P>;
-        using L = TmaLayout<P, 0, Fld::NF>;
+        using L = TmaLayout<P, 0, Fld>;
         const CompGrid& g = c.grid.c[0];
         TmaMaps maps;
         const void* f[3] = {c.r, c.dinv, pold};
