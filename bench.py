@@ -320,10 +320,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16-storage/f32"}[args.precision],
         "data": "synthetic (seeded dipole shell; stand-in for the paper's MAS Test 2 state)",
-        "config": {"workload": f"{args.workload}: {wl['n_r']}x{wl['n_t']}x{wl['n_p']} shell, thermal conduction + "
-                               f"3-component viscosity, {args.scheme.upper()} + PTL, dt = {wl['ratio']:g} dt_E per operator",
-                   "precision": args.precision, "scheme": args.scheme, "parallelism": f"replicas x{world}",
-                   "l2": "working set ~4 GB >> 129 MB L2: no flush needed"},
+        "config": arm_config(args, wl, world),
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
         "cpu_baseline": cpu, "step": step_stats, "kernels": kernels, "wall_s_timed": round(wall, 3),
         **extra,
@@ -720,6 +717,14 @@ def cpu_baseline(g, tc, vi, wl, step_stats, n_tc, n_v, budget_s=16.0):
             "tc_point_stages_per_s": rates["tc"][0], "visc_point_stages_per_s": rates["visc"][0]}
 
 
+def arm_config(args, wl, world):
+    """The workload description both arms print."""
+    return {"workload": f"{args.workload}: {wl['n_r']}x{wl['n_t']}x{wl['n_p']} shell, thermal conduction + "
+                        f"3-component viscosity, {args.scheme.upper()} + PTL, dt = {wl['ratio']:g} dt_E per operator",
+            "precision": args.precision, "scheme": args.scheme, "parallelism": f"replicas x{world}",
+            "l2": "working set ~4 GB >> 129 MB L2: no flush needed"}
+
+
 def run_reference(args):
     """The oracle as the reference arm: each step is a bounded sample of the workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -746,8 +751,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"{args.workload} (oracle window sample)",
-                                            "precision": "fp64", "scheme": "rkl2"},
+            "data": "synthetic", "config": arm_config(args, wl, int(os.environ.get("WORLD_SIZE", "1"))),
             "cpu_baseline": cpu, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                                          "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
