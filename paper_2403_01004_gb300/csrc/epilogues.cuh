@@ -42,6 +42,20 @@ struct LoadPcgP {
     }
 };
 
+// Order key of a non-negative value: its bit pattern as a signed integer orders like the value,
+// and Inf and NaN sort above every finite value (-1 is below every key).
+template <typename A> struct MagKey;
+template <> struct MagKey<float> {
+    using K = int;
+    __device__ static K of(float v) { return __float_as_int(v); }
+    __device__ static float value(K k) { return __int_as_float(k); }
+};
+template <> struct MagKey<double> {
+    using K = long long;
+    __device__ static K of(double v) { return __double_as_longlong(v); }
+    __device__ static double value(K k) { return __longlong_as_double(k); }
+};
+
 // ---- epilogues -----------------------------------------------------------------------------
 // F = w A u (stored), optionally the stage-1 increment d1 = a F (STS stage 1, see EpiStage)
 // and the block arg-max of |F|.
@@ -49,17 +63,20 @@ template <class P, bool ARGMAX, bool U1>
 struct EpiF {
     using A = typename P::A;
     using S = typename P::S;
+    using K = typename MagKey<A>::K;
     using Pre = NoPre;
     S* F;
     S* u1;
     A a;
     ArgMax* part;
     int* nonfinite;
-    A bv;            // running max |F| of this thread, compared in the arithmetic precision (the
-    long long bi;    // stored F converts exactly, so the decision equals a float64 comparison)
-    int bad;
+    // running max |F| of this thread as an order key of the arithmetic-precision value (the stored
+    // F converts exactly, so the decision equals a float64 comparison); one integer compare per
+    // point, non-finite values win it and are reported once at the end
+    K bk;
+    long long bi;
     static constexpr int NC = 0;     // point operands delivered by the TMA kernel
-    __device__ void init() { bv = A(-1); bi = LLONG_MAX; bad = 0; }
+    __device__ void init() { bk = K(-1); bi = LLONG_MAX; }
     __device__ bool skip() const { return false; }
     __device__ Pre prefetch(long long) const { return {}; }
     using E = typename P::E;
@@ -70,14 +87,14 @@ struct EpiF {
         F[idx] = fs;
         if (U1) u1[idx] = cvt<S>(a * f);
         if (ARGMAX) {
-            const A v = fabs(cvt<A>(fs));
-            if (!isfinite(v)) bad = 1;
-            else if (v > bv) { bv = v; bi = idx; }   // a thread visits its indices in rising order
+            const K key = MagKey<A>::of(fabs(cvt<A>(fs)));
+            if (key > bk) { bk = key; bi = idx; }    // a thread visits its indices in rising order
         }
     }
     __device__ void finish() {
         if (!ARGMAX) return;
-        if (bad) atomicOr(nonfinite, 1);
+        const A bv = bk < 0 ? A(-1) : MagKey<A>::value(bk);
+        if (bk >= 0 && !isfinite(bv)) atomicOr(nonfinite, 1);
         double v = (double)bv;
         long long i = bi;
         block_argmax(v, i);
