@@ -218,9 +218,9 @@ tc_march(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld_in,
 // the four in-plane neighbours (other threads' points, served by L1 / L2) and prefetches the
 // next plane's operands one iteration ahead.
 // ---------------------------------------------------------------------------------------------
-template <class P, class Load, class Epi, bool PER = false>
-__global__ void __launch_bounds__(NTHREADS)
-visc_march(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld_in, Epi ep_in) {
+template <class P, class Load, class Epi, bool PER>
+__device__ __forceinline__ void visc_march_body(const MarchGrid& g, const Coef4<typename P::C>* __restrict__ coef,
+                                                const Load& ld_in, const Epi& ep_in) {
     using A = typename P::A;
     using C = typename P::C;
 
@@ -289,6 +289,20 @@ visc_march(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld_i
         }
     }
     ep.finish();
+}
+
+template <class P, class Load, class Epi, bool PER = false>
+__global__ void __launch_bounds__(NTHREADS)
+visc_march(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld, Epi ep) {
+    visc_march_body<P, Load, Epi, PER>(g, coef, ld, ep);
+}
+
+// The same march with the register budget of 5 resident blocks per SM (48 registers): used where
+// that fits without spilling and the extra block hides memory latency (the float32 PTL pass).
+template <class P, class Load, class Epi, bool PER = false>
+__global__ void __launch_bounds__(NTHREADS, 5)
+visc_march_5(MarchGrid g, const Coef4<typename P::C>* __restrict__ coef, Load ld, Epi ep) {
+    visc_march_body<P, Load, Epi, PER>(g, coef, ld, ep);
 }
 
 }  // namespace pb

@@ -11,6 +11,11 @@
 
 namespace pb {
 
+// Epilogues whose viscosity march runs with the 5-blocks-per-SM register budget (checked free of
+// spills with -Xptxas -v): the float32 PTL pass.
+template <class Epi> struct ViscCapped { static constexpr bool value = false; };
+template <bool U1> struct ViscCapped<EpiF<PolF32, true, U1>> { static constexpr bool value = true; };
+
 template <class P>
 class OpsImpl : public Ops {
     using S = typename P::S;
@@ -26,6 +31,9 @@ class OpsImpl : public Ops {
         if (c.kind == PB_TC_ANISO) {
             if (box) tc_march<P, Load, Epi, true><<<c.grid.nblocks, block, 0, c.stream>>>(c.grid, cf, ld, ep);
             else tc_march<P, Load, Epi><<<c.grid.nblocks, block, 0, c.stream>>>(c.grid, cf, ld, ep);
+        } else if constexpr (ViscCapped<Epi>::value) {
+            if (box) visc_march_5<P, Load, Epi, true><<<c.grid.nblocks, block, 0, c.stream>>>(c.grid, cf, ld, ep);
+            else visc_march_5<P, Load, Epi><<<c.grid.nblocks, block, 0, c.stream>>>(c.grid, cf, ld, ep);
         } else {
             if (box) visc_march<P, Load, Epi, true><<<c.grid.nblocks, block, 0, c.stream>>>(c.grid, cf, ld, ep);
             else visc_march<P, Load, Epi><<<c.grid.nblocks, block, 0, c.stream>>>(c.grid, cf, ld, ep);
