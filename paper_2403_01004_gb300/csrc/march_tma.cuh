@@ -28,7 +28,7 @@ namespace pb {
 
 template <typename S> struct HaloPad { static constexpr int value = 16 / (int)sizeof(S); };
 
-constexpr int kSlots = 4;
+constexpr int kSlots = 3;
 
 __host__ __device__ constexpr int align128(int b) { return (b + 127) & ~127; }
 
