@@ -57,13 +57,11 @@ class OpsImpl : public Ops {
             for (int a = 0; ok && a < Epi::NC; ++a)
                 ok = tma_state_map(&maps.cen[a], cen[a], sizeof(S), g.nr, g.nt, g.np, TX, TY);
             if (ok) {
-                static bool attr = false;
                 const int smem = L::TOTAL + 128;
-                if (!attr) {
-                    PB_CUDA_TRY(cudaFuncSetAttribute(tc_march_tma<P, Epi, StateField>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-                    attr = true;
-                }
+                // once per kernel instantiation (a function-local static: thread-safe initialisation)
+                static const cudaError_t attr = cudaFuncSetAttribute(tc_march_tma<P, Epi, StateField>,
+                                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                PB_CUDA_TRY(attr);
                 tc_march_tma<P, Epi, StateField><<<c.grid.nblocks, dim3(TX, TY), smem, c.stream>>>(c.grid, maps, ep, c.d_err);
                 PB_CUDA_TRY(cudaGetLastError());
                 return;
@@ -84,13 +82,10 @@ class OpsImpl : public Ops {
         bool ok = tma_coef_map(&maps.coef, c.coef_be, sizeof(C), g.nr, g.nt, g.np, TX + 1, TY + 1);
         for (int a = 0; ok && a < 3; ++a) ok = tma_state_map(&maps.halo[a], f[a], sizeof(S), g.nr, g.nt, g.np, L::BXW, TY + 2);
         if (!ok) return false;
-        static bool attr = false;
         const int smem = L::TOTAL + 128;
-        if (!attr) {
-            PB_CUDA_TRY(cudaFuncSetAttribute(tc_march_tma<P, EpiPcgSpmv<P>, Fld>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-            attr = true;
-        }
+        static const cudaError_t attr = cudaFuncSetAttribute(tc_march_tma<P, EpiPcgSpmv<P>, Fld>,
+                                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        PB_CUDA_TRY(attr);
         tc_march_tma<P, EpiPcgSpmv<P>, Fld><<<c.grid.nblocks, dim3(TX, TY), smem, c.stream>>>(c.grid, maps, ep, c.d_err,
                                                                                              Fld{c.d_pcg, A(0), 0});
         PB_CUDA_TRY(cudaGetLastError());
