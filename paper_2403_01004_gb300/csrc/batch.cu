@@ -97,7 +97,10 @@ __device__ void run_item(const BatchProblem& pr, int L, int t, const LevelCoef* 
     }
 }
 
-__global__ void __launch_bounds__(NTHREADS)
+// 5 resident blocks per SM (48 registers; the spills are in the item dispatch, outside the
+// per-plane loop): one kernel carries every epilogue, and without the cap it takes 80 registers
+// and only 3 blocks fit on an SM
+__global__ void __launch_bounds__(NTHREADS, 5)
 batch_kernel(const BatchProblem* __restrict__ probs, const BatchSeg* __restrict__ segs, int nsegs, long long total,
              const LevelCoef* __restrict__ lc, unsigned long long* next, int* err) {
     __shared__ BatchSmem sm;
