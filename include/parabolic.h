@@ -210,6 +210,14 @@ PB_API int ptl_full_compute(pb_ctx* ctx, const void* u_dev, double* dt_full, int
 PB_API int rkl2_advance(pb_ctx* ctx, void* u_dev, double dt, const pb_advance_opts* opts,
                  pb_stats* stats);
 
+/* The graph-only form of rkl2_advance: the cycles of a forced schedule (opts->dt_cycles), or one
+ * cycle of length dt when opts->use_ptl is 0, enqueued on the context's stream.  It returns
+ * without waiting, reads nothing back to the host and allocates nothing, so it can be captured in
+ * a CUDA graph and replayed.  The PTL is refused with PB_EINVAL: it needs a host round trip per
+ * cycle.  No statistics; errors found on the device (a bounded wait that ran out) surface at the
+ * next synchronous call. */
+PB_API int rkl2_advance_async(pb_ctx* ctx, void* u_dev, double dt, const pb_advance_opts* opts);
+
 /* Advances u (device, in place) over dt with Backward Euler, each cycle solving
  * (M - dt_c A) x = M u (M = diag(1/w), F = w A u) by point-Jacobi PCG from x0 = u, or from
  * x0_dev (device, ctx precision) on the first cycle when it is not NULL.  Supported for

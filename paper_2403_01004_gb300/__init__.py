@@ -32,7 +32,7 @@ C_TC = (5.0 / 3.0 - 1.0) / 2.0
 # C function names exported by the library (kept in step with include/parabolic.h)
 EXPORTS = ("pb_advance_opts_init", "pb_status_string", "pb_last_error", "parabolic_setup",
            "parabolic_update", "parabolic_destroy", "parabolic_state_size", "parabolic_dt_explicit", "parabolic_apply",
-           "ptl_compute", "ptl_full_compute", "rkl2_advance", "be_pcg_advance", "pb_profile_enable", "pb_profile_read",
+           "ptl_compute", "ptl_full_compute", "rkl2_advance", "rkl2_advance_async", "be_pcg_advance", "pb_profile_enable", "pb_profile_read",
            "pb_ptl_noalloc", "pb_tune_init", "pb_batch_create", "pb_batch_destroy", "pb_batch_last_error",
            "pb_batch_rkl2_advance", "pb_autotune", "pb_model_create", "pb_model_destroy", "pb_model_last_error",
            "pb_model_num_params", "pb_model_get_params", "pb_model_set_params", "pb_model_save", "pb_model_load",
@@ -112,6 +112,8 @@ def load_library(path: str = LIB_PATH):
     lib.parabolic_apply.argtypes = [c_void_p, c_void_p, c_void_p]
     lib.ptl_compute.argtypes = [c_void_p, c_void_p, POINTER(c_double), POINTER(c_int64), POINTER(c_double)]
     lib.rkl2_advance.argtypes = [c_void_p, c_void_p, c_double, POINTER(PbAdvanceOpts), POINTER(PbStats)]
+    lib.rkl2_advance_async.argtypes = [c_void_p, c_void_p, c_double, POINTER(PbAdvanceOpts)]
+    lib.ptl_full_compute.argtypes = [c_void_p, c_void_p, POINTER(c_double), POINTER(c_int64), POINTER(c_int32)]
     lib.be_pcg_advance.argtypes = [c_void_p, c_void_p, c_double, POINTER(PbAdvanceOpts), c_void_p, POINTER(PbStats)]
     lib.pb_ptl_noalloc.argtypes = [c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
                                    POINTER(c_double), POINTER(c_int64), POINTER(c_double), c_void_p]
@@ -396,6 +398,15 @@ def rkl2_advance(ctx: Context, u, dt: float, scheme: str = "rkl2", use_ptl: bool
     if raise_on_error:
         _check(rc, ctx.handle)
     return d
+
+
+def rkl2_advance_async(ctx: Context, u, dt: float, scheme: str = "rkl2", forced=None, use_ptl: bool = True) -> None:
+    """Enqueues a forced schedule, or one cycle of dt with use_ptl=False, on the context's stream
+    and returns at once: no host reads, no allocation, capturable in a CUDA graph.  The PTL
+    (use_ptl without a forced schedule) is refused."""
+    _check_state(ctx, u)
+    o, keep = _opts(scheme, use_ptl, 0, 1.0, forced)
+    _check(load_library().rkl2_advance_async(ctx.handle, c_void_p(_ptr(u)), float(dt), byref(o)), ctx.handle)
 
 
 def be_pcg_advance(ctx: Context, u, dt: float, use_ptl: bool = True, forced=None, rtol: float = 1e-10,

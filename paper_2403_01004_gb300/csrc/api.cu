@@ -235,6 +235,23 @@ PtlResult run_ptl(Ctx& c, Ops* ops, const void* u, bool full = false) {
     return *c.h_ptl;
 }
 
+// The stages of one cycle of length dt_c (y0 = F(in) in c.y0) from `in` into `out`, in increment
+// form d_k = u_k - u_0 (see EpiStage): stages 1 and 2 fused (d1 = mut_1 dt y0 in buf[0]), d_k in
+// buf[(k-1) % 3], the last stage writes u_0 + d_s into out.  in == out is allowed: the last stage
+// reads u_0 at its own point only.  Enqueue only: no host reads, no allocation.
+void enqueue_stages(Ctx& c, Ops* ops, const Sts& co, double dt_c, const void* in, void* out) {
+    const double a1 = co.mut[1] * dt_c;
+    const StageCoef k2{co.mu[2], co.nu[2], co.mut[2] * dt_c, (co.mut[2] + co.gt[2]) * dt_c};
+    if (co.s == 2) ops->stage2(c, c.y0, nullptr, in, out, a1, k2);
+    else ops->stage2(c, c.y0, c.buf[0], nullptr, c.buf[1], a1, k2);
+    for (int k = 3; k <= co.s; ++k) {
+        const bool last = k == co.s;
+        ops->stage(c, c.buf[(k - 2) % 3], c.buf[(k - 3) % 3], last ? in : nullptr, c.y0,
+                   last ? out : c.buf[(k - 1) % 3],
+                   StageCoef{co.mu[k], co.nu[k], co.mut[k] * dt_c, (co.mut[k] + co.gt[k]) * dt_c});
+    }
+}
+
 // Decides the next cycle length (Sec. 2): returns false when the step is complete.
 struct CycleState {
     double dt, t_rem;
@@ -464,6 +481,30 @@ int ptl_full_compute(pb_ctx* h, const void* u, double* dt_full, int64_t* cell, i
     });
 }
 
+int rkl2_advance_async(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts) {
+    if (!h) return PB_EINVAL;
+    Ctx& c = h->c;
+    return guarded(&c, [&] {
+        const pb_advance_opts o = resolve(opts);
+        if (!u) throw Error{PB_EINVAL, "null state pointer"};
+        if (!(dt >= 0.0) || std::isinf(dt)) throw Error{PB_EINVAL, "dt must be finite and >= 0"};
+        const bool forced = o.n_forced > 0;
+        if (!forced && o.use_ptl)
+            throw Error{PB_EINVAL, "the PTL needs a host round trip per cycle: use rkl2_advance, or a forced schedule"};
+        Ops* ops = ops_of(c);
+        const int n = forced ? o.n_forced : 1;
+        Sts co;
+        for (int cycle = 0; cycle < n; ++cycle) {
+            const double dt_c = forced ? o.dt_cycles[cycle] : dt;
+            if (!(dt_c >= 0.0) || std::isinf(dt_c)) throw Error{PB_EINVAL, "cycle length must be finite and >= 0"};
+            if (dt_c == 0.0) continue;
+            make_sts(o.scheme, dt_c / c.dt_e, co);
+            ops->apply(c, u, c.y0);
+            enqueue_stages(c, ops, co, dt_c, u, u);
+        }
+    });
+}
+
 int rkl2_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, pb_stats* st) {
     if (!h) return PB_EINVAL;
     Ctx& c = h->c;
@@ -480,22 +521,7 @@ int rkl2_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, pb_
         const double floor_dt = o.ptl_floor * c.dt_e;
         double t_rem = dt;
         Sts co;
-        // the stages of one cycle of length dt_c (y0 = F(in) in c.y0) from `in` into `out`, in
-        // increment form d_k = u_k - u_0 (see EpiStage): stages 1 and 2 fused (d1 = mut_1 dt y0 in
-        // buf[0]), d_k in buf[(k-1) % 3], the last stage writes u_0 + d_s into out.  in == out is
-        // allowed: the last stage reads u_0 at its own point only.
-        auto stages = [&](double dt_c, const void* in, void* out) {
-            const double a1 = co.mut[1] * dt_c;
-            const StageCoef k2{co.mu[2], co.nu[2], co.mut[2] * dt_c, (co.mut[2] + co.gt[2]) * dt_c};
-            if (co.s == 2) ops->stage2(c, c.y0, nullptr, in, out, a1, k2);
-            else ops->stage2(c, c.y0, c.buf[0], nullptr, c.buf[1], a1, k2);
-            for (int k = 3; k <= co.s; ++k) {
-                const bool last = k == co.s;
-                ops->stage(c, c.buf[(k - 2) % 3], c.buf[(k - 3) % 3], last ? in : nullptr, c.y0,
-                           last ? out : c.buf[(k - 1) % 3],
-                           StageCoef{co.mu[k], co.nu[k], co.mut[k] * dt_c, (co.mut[k] + co.gt[k]) * dt_c});
-            }
-        };
+        auto stages = [&](double dt_c, const void* in, void* out) { enqueue_stages(c, ops, co, dt_c, in, out); };
         auto take = [&](const PtlResult& r, double& dtp, double& dfull, long long& kk) {
             if (r.nonfinite) throw Error{PB_ENONFINITE, "non-finite F in the PTL pass"};
             dtp = o.ptl_mode == PB_PTL_FULL ? r.dt_full : r.dt_ptl;

@@ -387,3 +387,34 @@ def test_be_mixed_precision_refinement(kind):
     ud = to_dev(u, ctx)
     st = pb.be_pcg_advance(ctx, ud, dt, use_ptl=True, rtol=1e-10, mixed=True)
     assert st["final_rel_residual"] <= 1e-10 and abs(st["cycles"] - log.cycles) <= 2
+
+
+@pytest.mark.parametrize("kind", ["tc", "visc"])
+def test_async_advance_replays_from_a_cuda_graph(kind):
+    """rkl2_advance_async (a forced schedule, enqueued only) captured in a CUDA graph and replayed
+    gives the synchronous call's result bit for bit; the PTL is refused by the graph-only form."""
+    import torch
+    import paper_2403_01004_gb300 as pb
+    from synth import device
+    g, inp, op, u = tc_problem(40, 21, 13) if kind == "tc" else visc_problem(24, 20, 16)
+    s = torch.cuda.Stream()
+    fields = device.tc_fields(inp) if kind == "tc" else device.visc_fields(inp)
+    ctx = pb.parabolic_setup(g.r_face, g.t_face, g.n_phi, kind, fields, "fp32", stream=s)
+    _, log = sts_advance(op, u, 50.0 * op.dt_explicit(), "rkl2", use_ptl=True)
+    sched = list(log.dt_c)
+    ref = to_dev(u, ctx)
+    torch.cuda.synchronize()
+    pb.rkl2_advance(ctx, ref, sum(sched), forced=sched)
+    x = to_dev(u, ctx)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        pb.rkl2_advance_async(ctx, x, 0.0, forced=sched)
+    for _ in range(2):
+        x.copy_(to_dev(u, ctx))
+        torch.cuda.synchronize()
+        graph.replay()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(to_host(x), to_host(ref))
+    with pytest.raises(pb.ParabolicError):
+        pb.rkl2_advance_async(ctx, x, 50.0 * op.dt_explicit())      # one cycle under the PTL
