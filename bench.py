@@ -30,6 +30,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -313,6 +315,8 @@ def run_ours(args):
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(g, tc, vi, wl, step_stats, n_tc, n_v)
+        cpu["cpu_model"] = cpu_model()
+        extra["cpu_baseline_all_cores"] = cpu_baseline_all_cores(g, tc, vi, step_stats, n_tc, n_v)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -703,6 +707,67 @@ def oracle_rates(g, tc, vi, budget_s: float):
             stages += s
         out[name] = (o.n * stages / (time.perf_counter() - t0), o.n, stages)
     return out
+
+
+def _window_rates(args):
+    """One process's share of the all-cores oracle timing: the conduction and viscosity stage
+    rates on its own 8-plane phi window (arrays sliced by the parent)."""
+    r_face, t_face, n_phi, T, n, B, rho, nu, v, budget_s = args
+    import numpy as np
+    from oracle.geometry import Shell
+    from oracle.sts import rkl2_coefficients, sts_step
+    from oracle.tc import TCOperator
+    from oracle.visc import ViscOperator
+    kw = T.shape[0]
+    sh = Shell(r_face, t_face, kw, dphi=2 * np.pi / n_phi)
+    ops = (("tc", TCOperator.spherical(sh, T, n, B), T.reshape(-1).copy()),
+           ("visc", ViscOperator.spherical(sh, rho, nu), np.concatenate([a.reshape(-1) for a in v])))
+    out = {}
+    for name, o, x in ops:
+        s, stages = 4, 0
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < budget_s / 2:
+            sts_step(o.apply, x, o.apply(x), 1e-9, rkl2_coefficients(s))
+            stages += s
+        out[name] = o.n * stages / (time.perf_counter() - t0)
+    return out
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def cpu_baseline_all_cores(g, tc, vi, step_stats, n_tc, n_v, budget_s=8.0):
+    """The oracle on every host core at once: one spawned process per core, each timing its own
+    8-plane phi window of the workload; the per-core rates add up."""
+    import multiprocessing as mp
+    ncores = os.cpu_count() or 1
+    kw = 8
+    jobs = []
+    for w in range(ncores):
+        ks = [(kw * w + d) % g.n_phi for d in range(kw)]
+        sl = lambda a: np.ascontiguousarray(a[ks])
+        jobs.append((g.r_face, g.t_face, g.n_phi, sl(tc.T), sl(tc.n), [sl(b) for b in tc.B],
+                     [sl(a) for a in vi.rho], [sl(a) for a in vi.nu], [sl(a) for a in vi.v], budget_s))
+    with mp.get_context("spawn").Pool(ncores) as pool:
+        res = pool.map(_window_rates, jobs)
+    r_tc = sum(r["tc"] for r in res)
+    r_v = sum(r["visc"] for r in res)
+    st = step_stats
+    t_est = n_tc * st["tc"]["stages"] / r_tc + n_v * st["visc"]["stages"] / r_v
+    return {"value": (n_tc * st["tc"]["stages"] + n_v * st["visc"]["stages"]) / t_est, "unit": UNIT,
+            "cores": ncores, "cpu_model": cpu_model(), "kind": "oracle",
+            "sample": f"{ncores} spawned processes, each the NumPy float64 oracle on its own 256x256x8 phi "
+                      f"window (~{budget_s:.0f} s); per-core rates summed, combined in the step's stage mix",
+            "tc_point_stages_per_s": r_tc, "visc_point_stages_per_s": r_v}
 
 
 def cpu_baseline(g, tc, vi, wl, step_stats, n_tc, n_v, budget_s=16.0):
