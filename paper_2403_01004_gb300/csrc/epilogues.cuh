@@ -415,15 +415,11 @@ ptl_finalize_kernel(MarchGrid g, const typename P::S* u, const typename P::S* F,
         argmax_merge(v, i, m.v, m.i);
     }
     block_argmax(v, i);
-    if (threadIdx.x != 0) return;
-    PtlResult out;
-    out.nonfinite = *nonfinite;
-    out.fmax = v;
-    out.k = i;
-    out.dt_ptl = 1.0 / 0.0;
-    out.pad = 0;
-    out.dt_full = __longlong_as_double(0x7ff8000000000000LL);
-    out.key_full = -1;
+    if (threadIdx.x >= 32) return;
+    // warp 0 holds the arg-max; Eq. 5 at k: lane a < nn takes neighbour a, so the six pairs of
+    // dependent loads are in flight together, and a warp min gives the smallest bound
+    const int lane = threadIdx.x;
+    double best = 1.0 / 0.0;
     if (i >= 0 && i != LLONG_MAX) {
         int comp = 0;
         for (int c = 1; c < g.ncomp; ++c)
@@ -448,15 +444,28 @@ ptl_finalize_kernel(MarchGrid g, const typename P::S* u, const typename P::S* F,
         else if (per) nb[nn++] = i - (long long)(cg.nt - 1) * cg.nr;
         nb[nn++] = cg.offset + (long long)((kk + cg.np - 1) % cg.np) * plane + rem;
         nb[nn++] = cg.offset + (long long)((kk + 1) % cg.np) * plane + rem;
-        const double uk = (double)cvt<A>(u[i]), fk = (double)cvt<A>(F[i]);
-        double best = 1.0 / 0.0;
-        for (int a = 0; a < nn; ++a) {
-            const double du = uk - (double)cvt<A>(u[nb[a]]);
-            const double df = fk - (double)cvt<A>(F[nb[a]]);
-            if (du != 0.0 && df != 0.0 && du * df < 0.0) best = fmin(best, -du / df);
+        if (lane < nn) {
+            long long j = nb[0];
+#pragma unroll
+            for (int a = 1; a < 6; ++a)
+                if (lane == a) j = nb[a];
+            const double uk = (double)cvt<A>(u[i]), fk = (double)cvt<A>(F[i]);
+            const double du = uk - (double)cvt<A>(u[j]);
+            const double df = fk - (double)cvt<A>(F[j]);
+            if (du != 0.0 && df != 0.0 && du * df < 0.0) best = -du / df;
         }
-        out.dt_ptl = best;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
     }
+    if (lane != 0) return;
+    PtlResult out;
+    out.nonfinite = *nonfinite;
+    out.fmax = v;
+    out.k = i;
+    out.dt_ptl = best;
+    out.pad = 0;
+    out.dt_full = __longlong_as_double(0x7ff8000000000000LL);
+    out.key_full = -1;
     *res = out;
 }
 
