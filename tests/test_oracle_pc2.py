@@ -11,10 +11,14 @@ oracle's 27-point row entries (checked against its matrix-free product).  Precon
   - symmetric Gauss-Seidel, (D + L) D^-1 (D + U), in the natural ordering;
   - the same two in the 8-colour ordering (colour = parity of (k, j, i)): with the 27-point
     stencil no two cells of one colour are coupled, so each triangular solve becomes 8 parallel
-    colour steps -- the form a GPU can run.
+    colour steps -- the form a GPU can run;
+  - block-local IC0 (PC2 as a distributed code applies it, ILU0 inside each subdomain): IC0 of S
+    without the couplings between blocks, for GPU-tile-sized 8 x 8 x 8 blocks and for blocks of
+    a third of the grid (16 phi x 24 theta x 24 r, a rank's subdomain).
 Run with -s to print the iteration counts.  The checks pin that every preconditioned solve
-reaches the same solution, that the factorisations save iterations in the natural order, and
-that the 8-colour order keeps less than a tenth of that saving."""
+reaches the same solution, that the factorisations save iterations in the natural order, that
+the 8-colour order keeps less than a tenth of that saving, and that block-local IC0 keeps it
+only with blocks far larger than a GPU tile."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -119,6 +123,16 @@ def _sgs_prec(S):
     return lambda r: spla.spsolve_triangular(upper, D * spla.spsolve_triangular(lower, r, lower=True), lower=False)
 
 
+def _block_local(S, shape, block):
+    """S without the entries that couple different blocks of size block = (bk, bj, bi)."""
+    k, j, i = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")
+    nb = [-(-n // b) for n, b in zip(shape, block)]
+    blk = (((k // block[0]) * nb[1] + j // block[1]) * nb[2] + i // block[2]).reshape(-1)
+    C = sp.coo_matrix(S)
+    keep = blk[C.row] == blk[C.col]
+    return sp.csr_matrix((C.data[keep], (C.row[keep], C.col[keep])), shape=S.shape)
+
+
 @pytest.fixture(scope="module")
 def system():
     g, inp, op, u = tc_problem(24, 24, 48)
@@ -164,6 +178,11 @@ def test_pc2_iteration_counts(system):
         # the same system solved: true residual at the tolerance, and x within cond(S) times it
         assert np.linalg.norm(b - S @ xs) <= 2e-10 * np.linalg.norm(b), name
         assert np.linalg.norm(xs - x_j) <= 1e-6 * np.linalg.norm(x_j), name
+    for name, block in (("block IC0, 8x8x8", (8, 8, 8)), ("block IC0, 16x24x24", (16, 24, 24))):
+        pre = _ic0_prec(_block_local(S, op.shape, block))
+        shifts[name] = pre.alpha
+        x, runs[name] = _pcg(S, b, u, pre, 1e-10)
+        assert np.linalg.norm(b - S @ x) <= 2e-10 * np.linalg.norm(b), name
     print()
     for name, it in runs.items():
         extra = f"  (IC0 of S + {shifts[name]:g} diag S)" if shifts.get(name) is not None else ""
@@ -173,3 +192,6 @@ def test_pc2_iteration_counts(system):
     # ... and the parallel 8-colour order keeps less than a tenth of that saving
     for name in ("IC0, 8 colours", "SGS, 8 colours"):
         assert runs[name] >= 0.9 * runs["point-Jacobi (PC1)"], name
+    # block-local IC0 keeps the saving only with blocks far larger than a GPU tile
+    assert runs["block IC0, 8x8x8"] >= 0.75 * runs["point-Jacobi (PC1)"]
+    assert runs["block IC0, 16x24x24"] <= 0.5 * runs["point-Jacobi (PC1)"]
