@@ -212,21 +212,32 @@ def run_ours(args):
         return step_tc(tc_fields, u_src) + step_visc(vi_fields, v_src)
 
     # end to end: every input from pinned host memory and both results back, inside the timed
-    # region; the viscosity inputs travel on a copy stream while conduction computes, and the
-    # conduction result while viscosity computes
+    # region, pipelined as a user advancing many steps would: the viscosity inputs travel on a
+    # copy stream while conduction computes, and the conduction result plus the next step's
+    # conduction inputs while viscosity computes (the first step of a timed run copies its own
+    # conduction inputs, the last prefetches none)
     copy_stream = torch.cuda.Stream()
+    e2e_state = {"left": 0, "tc_ready": None}
 
-    def e2e_step():
-        main = torch.cuda.current_stream()
-        copy_stream.wait_stream(main)
-        ev_tc, ev_v, ev_u = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
+    def copy_tc_inputs():
         with torch.cuda.stream(copy_stream):
             for k in ("T0", "n"):
                 d_tc[k].copy_(h_tc[k], non_blocking=True)
             for a in range(3):
                 d_tc["B"][a].copy_(h_tc["B"][a], non_blocking=True)
             d_u0.copy_(h_u, non_blocking=True)
-            ev_tc.record(copy_stream)
+            ev = torch.cuda.Event()
+            ev.record(copy_stream)
+        return ev
+
+    def e2e_step():
+        main = torch.cuda.current_stream()
+        e2e_state["left"] -= 1
+        copy_stream.wait_stream(main)
+        ev_tc = e2e_state["tc_ready"] or copy_tc_inputs()
+        e2e_state["tc_ready"] = None
+        ev_v, ev_u = torch.cuda.Event(), torch.cuda.Event()
+        with torch.cuda.stream(copy_stream):
             for a in range(3):
                 d_vi["rho"][a].copy_(h_vi["rho"][a], non_blocking=True)
                 d_vi["nu"][a].copy_(h_vi["nu"][a], non_blocking=True)
@@ -238,6 +249,8 @@ def run_ours(args):
         copy_stream.wait_event(ev_u)
         with torch.cuda.stream(copy_stream):
             out_u.copy_(u, non_blocking=True)
+        if e2e_state["left"] > 0:
+            e2e_state["tc_ready"] = copy_tc_inputs()
         main.wait_event(ev_v)
         units += step_visc(d_vi, d_v0)
         out_v.copy_(v, non_blocking=True)
@@ -284,7 +297,9 @@ def run_ours(args):
 
     e2e = None
     if not args.no_e2e:
+        e2e_state["left"] = 1
         e2e_step()
+        e2e_state["left"] = args.steps
         units_e, ms_e, _ = timed(e2e_step, args.steps)
         h2d = sum(t.numel() * t.element_size() for t in [h_tc["T0"], h_tc["n"], *h_tc["B"], *h_vi["rho"], *h_vi["nu"], h_u, h_v])
         d2h = out_u.numel() * out_u.element_size() + out_v.numel() * out_v.element_size()
