@@ -533,6 +533,34 @@ def learned_probe(pb, torch):
         torch.cuda.synchronize()
         out[name] = {"iterations": st["total_iters"], "ms": e0.elapsed_time(e1),
                      "rel_residual": st["final_rel_residual"], "started_from_guess": bool(st["guess_used"])}
+
+    def best_ms(fn, reps=5):
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return min(ts)
+
+    # the guess alone (features, four conv layers, x0) and the four tensor-core conv layers alone;
+    # per point a layer reads 16 bf16 channels and writes 16 (plus the 16 pre-activations of
+    # layers 1-3, the float32 output of layer 4), and does 27 x 16 x 16 multiply-adds
+    feats, _, _ = pb.pb_guess_features(ctx, u, dt)
+    shape = (1, g.n_phi, g.n_theta, g.n_r)
+    ms_guess = best_ms(lambda: pb.learned_guess(ctx, model, u, dt))
+    ms_net = best_ms(lambda: pb.pb_model_forward(model, feats, shape, wrap_d=True))
+    pts = ctx.n
+    flops = 4 * 2 * 27 * 16 * 16 * pts
+    layer_bytes = pts * (3 * (32 + 64) + (32 + 4))
+    out["guess_ms"] = ms_guess
+    out["network"] = {"ms": ms_net, "layers": 4, "points": pts, "TFLOP/s": flops / (ms_net / 1e3) / 1e12,
+                      "alg_GB/s": layer_bytes / (ms_net / 1e3) / 1e9,
+                      "note": "pb_model_forward: 4 tcgen05 conv layers (27 MMAs of 128 x 16 x 16 per 128 points), "
+                              "plus a device copy of the input features and of the output"}
     ctx.close()
     model.close()
     return {"what": "BE + PC1 PCG (mixed precision, rtol 1e-10), 192x192x384 shell, dt = 1e4 dt_E, one solve per guess",

@@ -11,7 +11,9 @@
 // the d (phi) axis may wrap.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <random>
@@ -20,6 +22,7 @@
 
 #include "epilogues.cuh"
 #include "launch.h"
+#include "umma.cuh"
 
 namespace pb {
 
@@ -49,6 +52,7 @@ struct Model {
     float* batch_mask = nullptr;
     double* loss_acc = nullptr;
     double* h_loss = nullptr;
+    int* d_err = nullptr;              // set by a conv kernel whose bounded wait ran out
     std::string err;
 };
 
@@ -152,6 +156,155 @@ conv_kernel(const __nv_bfloat16* __restrict__ in, int S, int D, int H, int W, in
     uint4* dst = reinterpret_cast<uint4*>(act_out + p * NC);
     dst[0] = *reinterpret_cast<uint4*>(&ob[0]);
     dst[1] = *reinterpret_cast<uint4*>(&ob[8]);
+}
+
+// The same layer on the tensor cores (tcgen05): per output tile of 2 (d) x 16 (h) x 8 (w) points,
+// each d slice is one M = 128, N = 16 accumulator in TMEM, summed over the 27 offsets by 27
+// MMAs of K = 16 (the input channels).  Row m of a slice is the point (h0 + m / 8, w0 + m % 8).
+// The input halo (4 x 18 x 10 points) sits in shared memory split by channel halves: plane c
+// holds channels 8c..8c+7 of every point, 16 bytes a point, w fastest.  For offset (a, b, c) the
+// A operand then starts at halo point (slice + a, b, c): its core matrices are the 8 consecutive
+// w points of one h row (rows 16 bytes apart), the next h row is 10 points (160 bytes) on, and
+// the second half of K is the other plane.  The weights of offset o are B = W[o] (N = co rows,
+// K = ci), stored the same way: 512 bytes per offset.  One thread issues the MMAs; the four
+// warps read the accumulators back (warp w owns TMEM lanes 32w..32w+31) and apply MODE's
+// epilogue.  CTAs walk the tiles grid-stride, allocating 32 TMEM columns once.
+constexpr int CT_D = 2, CT_H = 16, CT_W = 8;
+constexpr int CH_D = CT_D + 2, CH_H = CT_H + 2, CH_W = CT_W + 2;
+constexpr int CH_PTS = CH_D * CH_H * CH_W;
+constexpr int CA_PLANE = CH_PTS * 16;            // one channel-half plane of the halo (bytes)
+constexpr int CB_OFF = 2 * CA_PLANE;              // the weights follow the two planes
+constexpr int CONV_TC_SMEM = CB_OFF + 27 * 512;
+constexpr int CONV_TC_THREADS = 128;
+constexpr uint32_t kConvIdesc = umma::idesc_bf16_f32(128, 16);
+
+// 16-byte global -> shared copy; with valid == false nothing is read and 16 zero bytes land
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(CONV_TC_THREADS, 6)
+conv_tc_kernel(const __nv_bfloat16* __restrict__ in, int S, int D, int H, int W, int wrap_d,
+               const __nv_bfloat16* __restrict__ wt, const float* __restrict__ bias, __nv_bfloat16* pre_out,
+               __nv_bfloat16* act_out, float* fout, const __nv_bfloat16* __restrict__ mask_pre, int* err) {
+    extern __shared__ __align__(16) unsigned char smem[];     // descriptors need 16-byte alignment
+    __shared__ uint32_t tbase;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ float bias_s[NC];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* a_s = smem;
+    unsigned char* b_s = smem + CB_OFF;
+    if (MODE != 2 && tid < NC) bias_s[tid] = bias[tid];
+    for (int q = tid; q < NW; q += CONV_TC_THREADS) {
+        const int o = q / (NC * NC), ci = (q / NC) % NC, co = q % NC;
+        *reinterpret_cast<__nv_bfloat16*>(b_s + o * 512 + (ci / 8) * 256 + (co / 8) * 128 + (co % 8) * 16 + (ci % 8) * 2) =
+            wt[q];
+    }
+    __syncwarp();
+    if (warp == 0) umma::tmem_alloc(&tbase, 32);
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tb = tbase;
+    const int nbw = (W + CT_W - 1) / CT_W, nbh = (H + CT_H - 1) / CT_H, nbd = (D + CT_D - 1) / CT_D;
+    const long long ntiles = (long long)S * nbd * nbh * nbw;
+    unsigned phase = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        long long b = t;
+        const int bw = (int)(b % nbw); b /= nbw;
+        const int bh = (int)(b % nbh); b /= nbh;
+        const int bd = (int)(b % nbd);
+        const int s = (int)(b / nbd);
+        const int w0 = bw * CT_W, h0 = bh * CT_H, d0 = bd * CT_D;
+        // the halo by cp.async (all of a thread's copies in flight at once); points outside the
+        // grid are zero-filled (source size 0)
+        for (int q = tid; q < CH_PTS; q += CONV_TC_THREADS) {
+            const int xw = q % CH_W, xh = (q / CH_W) % CH_H, xd = q / (CH_W * CH_H);
+            int gd = d0 - 1 + xd;
+            const int gh = h0 - 1 + xh, gw = w0 - 1 + xw;
+            if (wrap_d) gd = (gd + D) % D;
+            const bool inside = gd >= 0 && gd < D && gh >= 0 && gh < H && gw >= 0 && gw < W;
+            const __nv_bfloat16* src = inside ? in + pidx(s, gd, gh, gw, D, H, W) * NC : in;
+            cp_async16(a_s + q * 16, src, inside);
+            cp_async16(a_s + CA_PLANE + q * 16, src + 8, inside);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        umma::fence_async_smem();
+        umma::fence_before_sync();
+        __syncthreads();
+        umma::fence_after_sync();
+        if (tid == 0) {
+            const uint32_t a0 = smem_u32(a_s), b0 = smem_u32(b_s);
+            for (int sl = 0; sl < CT_D; ++sl)
+                for (int o = 0; o < 27; ++o) {
+                    const int od = o / 9, oh = (o / 3) % 3, ow = o % 3;
+                    const uint32_t aa = a0 + (uint32_t)((((sl + od) * CH_H + oh) * CH_W + ow) * 16);
+                    umma::mma_bf16(tb + (uint32_t)(sl * 16), umma::smem_desc(aa, CA_PLANE, CH_W * 16),
+                                   umma::smem_desc(b0 + (uint32_t)(o * 512), 256, 128), kConvIdesc, o > 0);
+                }
+            umma::commit(&bar);
+        }
+        // every thread waits (bounded) for the MMAs; the outcome is made block-uniform
+        const int ok = __syncthreads_and(mbar_wait(&bar, phase) ? 1 : 0);
+        phase ^= 1u;
+        if (!ok) {
+            // give the tensor core one more bounded interval before TMEM is released
+            if (tid == 0) atomicExch(err, 1);
+            mbar_wait(&bar, phase ^ 1u);
+            break;
+        }
+        umma::fence_after_sync();
+        // both slices are read before any lane branches (the loads are warp-collective)
+        float accs[CT_D][NC];
+#pragma unroll
+        for (int sl = 0; sl < CT_D; ++sl)
+            umma::ld_32x32b_x16(tb + ((uint32_t)(32 * warp) << 16) + (uint32_t)(sl * 16), accs[sl]);
+        for (int sl = 0; sl < CT_D; ++sl) {
+            const float* acc = accs[sl];
+            const int m = 32 * warp + lane;
+            const int d = d0 + sl, h = h0 + m / CT_W, w = w0 + m % CT_W;
+            if (d >= D || h >= H || w >= W) continue;
+            const long long p = pidx(s, d, h, w, D, H, W);
+            if (MODE == 1) {
+                fout[p] = acc[0] + bias_s[0];
+                continue;
+            }
+            __align__(16) __nv_bfloat16 ob[NC];
+            if (MODE == 0) {
+                __align__(16) __nv_bfloat16 pb_[NC];
+#pragma unroll
+                for (int co = 0; co < NC; ++co) {
+                    const float z = acc[co] + bias_s[co];
+                    pb_[co] = __float2bfloat16_rn(z);
+                    ob[co] = __float2bfloat16_rn(fmaxf(z, 0.f));
+                }
+                if (pre_out) {
+                    uint4* dst = reinterpret_cast<uint4*>(pre_out + p * NC);
+                    dst[0] = *reinterpret_cast<uint4*>(&pb_[0]);
+                    dst[1] = *reinterpret_cast<uint4*>(&pb_[8]);
+                }
+            } else {
+                const __nv_bfloat16* mp = mask_pre + p * NC;
+#pragma unroll
+                for (int co = 0; co < NC; ++co) ob[co] = __float2bfloat16_rn(__bfloat162float(mp[co]) > 0.f ? acc[co] : 0.f);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(act_out + p * NC);
+            dst[0] = *reinterpret_cast<uint4*>(&ob[0]);
+            dst[1] = *reinterpret_cast<uint4*>(&ob[8]);
+        }
+        // the halo planes and the accumulators are reused by the next tile
+        umma::fence_before_sync();
+        __syncthreads();
+        umma::fence_after_sync();
+    }
+    if (warp == 0) umma::tmem_dealloc(tb, 32);
 }
 
 // dW[off][ci][co] += sum_p in[p + off][ci] g[p][co], db[co] += sum_p g[p][co] over one tile.
@@ -371,29 +524,80 @@ void ensure_ws(Model& m, long long pts) {
 }
 
 void set_attr() {
-    static bool done = false;
-    if (done) return;
-    PB_CUDA_TRY(cudaFuncSetAttribute(conv_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem()));
-    PB_CUDA_TRY(cudaFuncSetAttribute(conv_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem()));
-    PB_CUDA_TRY(cudaFuncSetAttribute(conv_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem()));
-    done = true;
+    // once per process (a function-local static: thread-safe initialisation)
+    static const cudaError_t e = [] {
+        cudaError_t r = cudaFuncSetAttribute(conv_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem());
+        if (r == cudaSuccess) r = cudaFuncSetAttribute(conv_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem());
+        if (r == cudaSuccess) r = cudaFuncSetAttribute(conv_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem());
+        return r;
+    }();
+    PB_CUDA_TRY(e);
+}
+
+// The tensor-core layer is the default; PB_CONV_CUDA_CORES=1 selects the CUDA-core kernel (same
+// layer, float32 FMAs), kept as the second implementation the tests compare it with.
+bool conv_on_cuda_cores() {
+    static const bool v = [] {
+        const char* e = getenv("PB_CONV_CUDA_CORES");
+        return e && e[0] == '1';
+    }();
+    return v;
+}
+
+int conv_tc_grid(long long ntiles) {
+    static const int sms = [] {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            n = 1;
+        }
+        return std::max(1, n);
+    }();
+    return (int)std::min<long long>(ntiles, (long long)sms * 6);   // 6 CTAs per SM fit its shared memory
+}
+
+// One conv layer (see conv_kernel / conv_tc_kernel for MODE).
+template <int MODE>
+void conv(Model& m, const __nv_bfloat16* in, int S, int D, int H, int W, int wrap, const __nv_bfloat16* wt,
+          const float* bias, __nv_bfloat16* pre, __nv_bfloat16* act, float* fout, const __nv_bfloat16* mask,
+          cudaStream_t st) {
+    if (conv_on_cuda_cores()) {
+        set_attr();
+        conv_kernel<MODE><<<nblocks3(S, D, H, W), 256, conv_smem(), st>>>(in, S, D, H, W, wrap, wt, bias, pre, act, fout,
+                                                                          mask);
+    } else {
+        // the largest shared-memory carve-out, so that 6 CTAs (36.9 KB each) fit an SM
+        static const cudaError_t carve = cudaFuncSetAttribute(conv_tc_kernel<MODE>,
+                                                              cudaFuncAttributePreferredSharedMemoryCarveout,
+                                                              (int)cudaSharedmemCarveoutMaxShared);
+        PB_CUDA_TRY(carve);
+        const long long ntiles = (long long)S * ((D + CT_D - 1) / CT_D) * ((H + CT_H - 1) / CT_H) * ((W + CT_W - 1) / CT_W);
+        conv_tc_kernel<MODE><<<conv_tc_grid(ntiles), CONV_TC_THREADS, CONV_TC_SMEM, st>>>(
+            in, S, D, H, W, wrap, wt, bias, pre, act, fout, mask, m.d_err);
+    }
+    PB_CUDA_TRY(cudaGetLastError());
+}
+
+// After a stream synchronisation: a conv kernel whose bounded wait for its MMAs ran out.
+void check_conv(Model& m) {
+    int e = 0;
+    PB_CUDA_TRY(cudaMemcpy(&e, m.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        PB_CUDA_TRY(cudaMemset(m.d_err, 0, sizeof(int)));
+        throw Error{PB_ETIMEOUT, "a tensor-core conv layer timed out waiting for its MMAs"};
+    }
 }
 
 // Forward over act[0] (already in place); keeps pre-activations for the backward pass.
 void forward(Model& m, int S, int D, int H, int W, int wrap, cudaStream_t st) {
-    set_attr();
-    const int nb = nblocks3(S, D, H, W);
     for (int l = 0; l < NL; ++l) {
         const __nv_bfloat16* wl = m.wfwd + (size_t)l * NW;
         const float* bl = m.master + (size_t)l * (NW + NC) + NW;
         if (l < NL - 1)
-            conv_kernel<0><<<nb, 256, conv_smem(), st>>>(m.act[l], S, D, H, W, wrap, wl, bl, m.pre[l], m.act[l + 1],
-                                                         nullptr, nullptr);
+            conv<0>(m, m.act[l], S, D, H, W, wrap, wl, bl, m.pre[l], m.act[l + 1], nullptr, nullptr, st);
         else
-            conv_kernel<1><<<nb, 256, conv_smem(), st>>>(m.act[l], S, D, H, W, wrap, wl, bl, nullptr, nullptr, m.out,
-                                                         nullptr);
+            conv<1>(m, m.act[l], S, D, H, W, wrap, wl, bl, nullptr, nullptr, m.out, nullptr, st);
     }
-    PB_CUDA_TRY(cudaGetLastError());
 }
 
 // Loss and gradients for the batch held in act[0] / batch_target / batch_mask; returns loss.
@@ -411,14 +615,14 @@ double backward(Model& m, int S, int D, int H, int W, double msum, cudaStream_t 
         wgrad_kernel<<<nb, 256, 0, st>>>(m.act[l], g, S, D, H, W, dW, dW + NW);
         if (l > 0) {
             // gradient wrt act[l] (= relu(pre[l-1])), masked by pre[l-1] > 0
-            conv_kernel<2><<<nb, 256, conv_smem(), st>>>(g, S, D, H, W, 0, m.wbwd + (size_t)l * NW, nullptr, nullptr, gn,
-                                                         nullptr, m.pre[l - 1]);
+            conv<2>(m, g, S, D, H, W, 0, m.wbwd + (size_t)l * NW, nullptr, nullptr, gn, nullptr, m.pre[l - 1], st);
             std::swap(g, gn);
         }
     }
     PB_CUDA_TRY(cudaGetLastError());
     PB_CUDA_TRY(cudaMemcpyAsync(m.h_loss, m.loss_acc, sizeof(double), cudaMemcpyDeviceToHost, st));
     PB_CUDA_TRY(cudaStreamSynchronize(st));
+    check_conv(m);
     return *m.h_loss / msum;
 }
 
@@ -458,7 +662,7 @@ int mguard(Model* m, F&& f) {
 
 void free_model(Model* m) {
     void* p[] = {m->master, m->m, m->v, m->grad, m->wfwd, m->wbwd, m->out, m->g0, m->g1, m->batch_target,
-                 m->batch_mask, m->loss_acc};
+                 m->batch_mask, m->loss_acc, m->d_err};
     for (void* q : p) if (q) cudaFree(q);
     for (auto* q : m->act) if (q) cudaFree(q);
     for (auto* q : m->pre) if (q) cudaFree(q);
@@ -513,6 +717,8 @@ int pb_model_create(uint64_t seed, pb_model** out) {
             PB_CUDA_TRY(cudaMalloc(&m.wfwd, NL * NW * sizeof(__nv_bfloat16)));
             PB_CUDA_TRY(cudaMalloc(&m.wbwd, NL * NW * sizeof(__nv_bfloat16)));
             PB_CUDA_TRY(cudaMalloc(&m.loss_acc, sizeof(double)));
+            PB_CUDA_TRY(cudaMalloc(&m.d_err, sizeof(int)));
+            PB_CUDA_TRY(cudaMemset(m.d_err, 0, sizeof(int)));
             PB_CUDA_TRY(cudaMallocHost(&m.h_loss, sizeof(double)));
             PB_CUDA_TRY(cudaMemset(m.m, 0, NPAR * sizeof(float)));
             PB_CUDA_TRY(cudaMemset(m.v, 0, NPAR * sizeof(float)));
@@ -618,6 +824,7 @@ int pb_model_forward(pb_model* h, const void* feats, int32_t S, int32_t D, int32
         forward(m, S, D, H, W, wrap_d, st);
         PB_CUDA_TRY(cudaMemcpyAsync(out, m.out, pts * sizeof(float), cudaMemcpyDeviceToDevice, st));
         PB_CUDA_TRY(cudaStreamSynchronize(st));
+        check_conv(m);
     });
 }
 
@@ -723,6 +930,7 @@ int learned_guess(pb_ctx* hc, pb_model* hm, const void* u, double dt, void* x0) 
             guess_kernel<PolF32><<<blocks, 256, 0, c.stream>>>(pts, static_cast<const float*>(u), m.out, S, static_cast<float*>(x0));
         PB_CUDA_TRY(cudaGetLastError());
         PB_CUDA_TRY(cudaStreamSynchronize(c.stream));
+        check_conv(m);
         return PB_OK;
     } catch (const Error& e) {
         c.err = e.msg;

@@ -136,3 +136,51 @@ def test_training_and_what_the_guess_gains(capsys):
     with capsys.disabled():
         print("\nPCG iterations to rtol 1e-10 (zero / previous-step / learned / learned judged):",
               [(r["zero"], r["previous"], r["learned"], r["learned+judge"]) for r in rows])
+
+
+_CONV_CASE = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, {tests!r})
+import paper_2403_01004_gb300 as pb
+from test_gpu_learned import _random_params
+rng = np.random.default_rng(11)
+params = _random_params(rng)
+model = pb.Model(1)
+model.set_params(params)
+S_, D, H, W = 2, 5, 19, 13
+f = np.zeros((S_, D, H, W, 16), np.float32)
+f[..., :6] = rng.normal(size=(S_, D, H, W, 6))
+fb = torch.from_numpy(f).bfloat16().cuda().reshape(-1)
+y0 = pb.pb_model_forward(model, fb, (S_, D, H, W), wrap_d=False).cpu().numpy()
+y1 = pb.pb_model_forward(model, fb, (S_, D, H, W), wrap_d=True).cpu().numpy()
+t = torch.from_numpy(rng.normal(size=(S_, D, H, W)).astype(np.float32)).cuda().reshape(-1)
+mask = torch.ones(S_ * D * H * W, dtype=torch.float32, device="cuda")
+L, g = pb.pb_model_grad(model, fb, t, mask, (S_, D, H, W))
+np.savez({out!r}, y0=y0, y1=y1, L=L, g=g)
+"""
+
+
+def test_tensor_core_layers_match_cuda_core_layers(tmp_path):
+    """The tcgen05 conv layers (the default) against the CUDA-core kernel of the same layers,
+    selected by PB_CONV_CUDA_CORES=1 in a second process: forward outputs (with and without the
+    phi wrap) and all gradients on a shape ragged in every tile dimension (2 x 5 x 19 x 13 against
+    output tiles of 2 x 16 x 8) agree to the rounding of their different summation orders (both
+    accumulate in float32; activations are rounded to bfloat16 between layers)."""
+    import os
+    import subprocess
+    import sys
+    tests = os.path.dirname(os.path.abspath(__file__))
+    res = {}
+    for name, env in (("tc", {}), ("cuda_cores", {"PB_CONV_CUDA_CORES": "1"})):
+        out = str(tmp_path / f"{name}.npz")
+        code = _CONV_CASE.format(tests=tests, out=out)
+        r = subprocess.run([sys.executable, "-c", code], env={**os.environ, **env}, capture_output=True, text=True,
+                           timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        res[name] = np.load(out)
+    a, b = res["tc"], res["cuda_cores"]
+    for key in ("y0", "y1"):
+        assert np.linalg.norm(a[key] - b[key]) <= 5e-3 * np.linalg.norm(b[key]), key
+    assert not np.allclose(a["y0"], a["y1"])        # the wrap changes the d-boundary points
+    assert float(a["L"]) == pytest.approx(float(b["L"]), rel=5e-3)
+    assert np.linalg.norm(a["g"] - b["g"]) <= 2e-2 * np.linalg.norm(b["g"])
