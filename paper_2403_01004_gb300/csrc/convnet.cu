@@ -240,24 +240,37 @@ conv_tc_kernel(const __nv_bfloat16* __restrict__ in, int S, int D, int H, int W,
         umma::fence_before_sync();
         __syncthreads();
         umma::fence_after_sync();
+        __shared__ int mma_ok;
         if (tid == 0) {
-            const uint32_t a0 = smem_u32(a_s), b0 = smem_u32(b_s);
-            for (int sl = 0; sl < CT_D; ++sl)
-                for (int o = 0; o < 27; ++o) {
+            // descriptors of offset 0; the start-address field counts 16-byte units, so moving the
+            // operand by a multiple of 16 bytes is an add on the descriptor (shared memory stays
+            // below 256 KB, so the 14-bit field cannot carry)
+            const uint64_t da0 = umma::smem_desc(smem_u32(a_s), CA_PLANE, CH_W * 16);
+            const uint64_t db0 = umma::smem_desc(smem_u32(b_s), 256, 128);
+            // the slices' accumulations interleaved: consecutive MMAs write different
+            // accumulators, so each does not wait for the one before it
+#pragma unroll
+            for (int o = 0; o < 27; ++o)
+#pragma unroll
+                for (int sl = 0; sl < CT_D; ++sl) {
                     const int od = o / 9, oh = (o / 3) % 3, ow = o % 3;
-                    const uint32_t aa = a0 + (uint32_t)((((sl + od) * CH_H + oh) * CH_W + ow) * 16);
-                    umma::mma_bf16(tb + (uint32_t)(sl * 16), umma::smem_desc(aa, CA_PLANE, CH_W * 16),
-                                   umma::smem_desc(b0 + (uint32_t)(o * 512), 256, 128), kConvIdesc, o > 0);
+                    umma::mma_bf16(tb + (uint32_t)(sl * 16), da0 + (uint64_t)(((sl + od) * CH_H + oh) * CH_W + ow),
+                                   db0 + (uint64_t)(o * 32), kConvIdesc, o > 0);
                 }
             umma::commit(&bar);
+            // one thread waits (bounded) for the MMAs; the others wait at the barrier
+            mma_ok = mbar_wait(&bar, phase) ? 1 : 0;
         }
-        // every thread waits (bounded) for the MMAs; the outcome is made block-uniform
-        const int ok = __syncthreads_and(mbar_wait(&bar, phase) ? 1 : 0);
+        __syncthreads();
+        const int ok = mma_ok;
         phase ^= 1u;
         if (!ok) {
             // give the tensor core one more bounded interval before TMEM is released
-            if (tid == 0) atomicExch(err, 1);
-            mbar_wait(&bar, phase ^ 1u);
+            if (tid == 0) {
+                atomicExch(err, 1);
+                mbar_wait(&bar, phase ^ 1u);
+            }
+            __syncthreads();
             break;
         }
         umma::fence_after_sync();
