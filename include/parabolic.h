@@ -316,7 +316,11 @@ PB_API int pb_model_load(pb_model* model, const char* path);
  * training target (x - u)/S is written too (float32); x and target are both NULL or both set. */
 PB_API int pb_guess_features(pb_ctx* ctx, const void* u, double dt, const void* x, void* feats, void* target,
                              double* scale);
-/* Network output for S_ samples of D x H x W feature points (wrap_d: periodic first axis). */
+/* Network output for S_ samples of D x H x W feature points (wrap_d: periodic first axis).
+ * The conv layers run on the tensor cores (tcgen05); environment PB_CONV_CUDA_CORES=1, read once
+ * per process, selects the CUDA-core kernel of the same layers instead.  PB_ETIMEOUT: a layer's
+ * bounded wait for its tensor-core operations ran out (the result is not valid).  The same holds
+ * for pb_model_grad, pb_model_train and learned_guess, which run the same layers. */
 PB_API int pb_model_forward(pb_model* model, const void* feats, int32_t S_, int32_t D, int32_t H, int32_t W,
                             int32_t wrap_d, void* out, void* stream);
 /* Mean-squared-error loss over mask and its gradient (host float32, pb_model_num_params()). */
