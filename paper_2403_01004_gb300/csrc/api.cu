@@ -211,8 +211,14 @@ void update_coefficients(Ctx& c, const pb_operator& op) {
         else setup_visc(c, op, c.coef64, &c.dt_e);
         ops_of(c)->store_coefs(c, c.coef64, c.s64);
     }
+    mixed_refresh(c);      // the float32 / double-float shadow of mixed-precision BE, if built
     sync(c);
     if (!(c.dt_e > 0.0) || std::isinf(c.dt_e)) throw Error{PB_ENONFINITE, "dt_E is not a positive finite number"};
+}
+
+bool env_on(const char* name) {
+    const char* e = getenv(name);
+    return e && e[0] == '1';
 }
 
 // The next cycle's length (Sec. 2): n = ceil(t_rem / max(dt_PTL, floor)) cycles remain and the
@@ -652,10 +658,18 @@ int be_pcg_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, c
             hs.fixed = o.fixed_iters > 0 ? o.fixed_iters : 0;
             hs.dt = dt_c;
             const PcgScalars hs0 = hs;
-            auto init = [&] {
+            // mixed precision on conduction: the residuals that drive the refinements in
+            // double-float arithmetic on the float32 pipes (about 48 bits), and a stop accepted only
+            // once the float64 residual confirms it (PB_MIXED_FP64_RESIDUAL=1: float64 throughout)
+            const bool df_residual = o.mixed_precision && c.prec == PB_FP64 && o.fixed_iters <= 0 &&
+                                     c.kind == PB_TC_ANISO && !env_on("PB_MIXED_FP64_RESIDUAL");
+            bool exact = true;      // the residual at hand is the float64 one
+            auto init = [&](bool want_exact = false) {
                 *c.h_pcg = hs0;
                 PB_CUDA_TRY(cudaMemcpyAsync(c.d_pcg, c.h_pcg, sizeof(PcgScalars), cudaMemcpyHostToDevice, c.stream));
-                ops->pcg_init(c, u, c.buf[0], dt_c);
+                exact = want_exact || !df_residual;
+                if (exact) ops->pcg_init(c, u, c.buf[0], dt_c);
+                else mixed_residual(c, u, c.buf[0], dt_c);
                 PB_CUDA_TRY(cudaMemcpyAsync(c.h_pcg, c.d_pcg, sizeof(PcgScalars), cudaMemcpyDeviceToHost, c.stream));
                 sync(c);
                 return c.h_pcg->rr;
@@ -683,6 +697,10 @@ int be_pcg_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, c
                     const PcgScalars now = *c.h_pcg;
                     if (now.done == 2) break;
                     if (now.rr <= now.tol2 * now.bb) {
+                        if (!exact) {       // confirm the stop on the float64 residual
+                            init(true);
+                            continue;
+                        }
                         c.h_pcg->done = 1;
                         break;
                     }

@@ -52,6 +52,8 @@ int reduce_blocks(const Ctx& c);   // grid size of the element-wise reduction ke
 
 // mixed-precision Backward Euler (mixed.cu)
 Ctx& mixed_shadow(Ctx& c);
+void mixed_refresh(Ctx& c);            // the shadow's records from the current float64 ones
+void mixed_residual(Ctx& c, const void* x, const void* un, double dt);   // conduction, double-float
 void free_shadow(Ctx* s);
 long long mixed_inner(Ctx& c, void* x, double dt, double inner_rtol, long long max_iter, int check_every, int* status);
 

@@ -11,9 +11,141 @@
 
 #include "epilogues.cuh"
 #include "launch.h"
+#include "march.cuh"
 
 namespace pb {
+
+// ---- double-float arithmetic -------------------------------------------------------------------
+// A value held as the unevaluated sum hi + lo of two floats (|lo| <= ulp(hi) / 2), about 48
+// significant bits, computed on the float32 pipes (GB300 issues float64 at a small fraction of
+// the float32 rate).  Sums follow Knuth's two-sum and Dekker's fast two-sum (the accurate
+// double-float addition); products take the exact rounding error of hi * hi from a fused
+// multiply-add.  Every operation is an explicit round-to-nearest intrinsic, so the compiler
+// neither contracts nor reorders the error terms.
+struct dfloat {
+    float hi, lo;
+    dfloat() = default;
+    __device__ constexpr dfloat(float h) : hi(h), lo(0.f) {}
+    __device__ constexpr dfloat(float h, float l) : hi(h), lo(l) {}
+};
+
+__device__ __forceinline__ dfloat two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return dfloat(s, e);
+}
+__device__ __forceinline__ dfloat fast_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return dfloat(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ dfloat operator+(dfloat x, dfloat y) {
+    dfloat s = two_sum(x.hi, y.hi);
+    const dfloat t = two_sum(x.lo, y.lo);
+    s = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ dfloat operator-(dfloat x) { return dfloat(-x.hi, -x.lo); }
+__device__ __forceinline__ dfloat operator-(dfloat x, dfloat y) { return x + (-y); }
+__device__ __forceinline__ dfloat operator*(dfloat x, dfloat y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ double to_double(dfloat x) { return (double)x.hi + (double)x.lo; }
+
+// float64 storage, double-float records and stencil arithmetic: the conduction residual of
+// mixed-precision Backward Euler (the kernel templates of the march take it as a policy)
+struct PolDF { using S = double; using C = dfloat; using A = dfloat; using E = double;
+               static constexpr int id = PB_FP64; static constexpr bool CG = false; };
+
+template <> __device__ __forceinline__ dfloat cvt<dfloat, double>(double v) {
+    const float h = __double2float_rn(v);
+    return dfloat(h, __double2float_rn(v - (double)h));
+}
+template <> __device__ __forceinline__ Coef4<dfloat> load_coef<dfloat, dfloat>(const Coef4<dfloat>* p) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+    const float4 x = __ldg(q), y = __ldg(q + 1);
+    return Coef4<dfloat>{dfloat(x.x, x.y), dfloat(x.z, x.w), dfloat(y.x, y.y), dfloat(y.z, y.w)};
+}
+
 namespace {
+
+// r = b - S x = M (u^n - x) + dt A x for the outer test of mixed-precision BE, with A x from the
+// double-float march and the rest in float64, and the sums <r, r>, <b, b>; the last block
+// writes the outer scalar state (as the float64 set-up pass does, without D^-1 and <r, D^-1 r>,
+// which the float32 inner solves form themselves).
+struct EpiResidualDF {
+    struct Pre { double un, x; };
+    const double* un;
+    const double* x;
+    double* r;
+    double dt;
+    PcgScalars* sc;
+    double* part;
+    unsigned int* counter;
+    int nblocks;
+    double acc[2];
+    __device__ void init() { acc[0] = acc[1] = 0.0; }
+    __device__ bool skip() const { return false; }
+    __device__ Pre prefetch(long long idx) const { return Pre{__ldg(un + idx), __ldg(x + idx)}; }
+    __device__ void apply(long long idx, dfloat Au, dfloat m, dfloat, const Pre& p) {
+        const double md = to_double(m);
+        const double rv = md * (p.un - p.x) + dt * to_double(Au);
+        r[idx] = rv;
+        const double b = md * p.un;
+        acc[0] += rv * rv;
+        acc[1] += b * b;
+    }
+    __device__ void finish() {
+        block_sum<2>(acc);
+        const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+        if (tid == 0) {
+            part[blockIdx.x * 4 + 0] = acc[0];
+            part[blockIdx.x * 4 + 1] = acc[1];
+        }
+        if (last_block(counter, nblocks)) {
+            double v[2];
+            sum_partials<2>(part, nblocks, 4, v);
+            if (tid == 0) {
+                sc->rz = 0.0;
+                sc->rr = v[0];
+                sc->bb = v[1];
+                sc->iter = 0;
+                sc->first = 1;
+                sc->beta = 0.0;
+                sc->alpha = 0.0;
+                int done = 0;
+                if (!(v[0] == v[0]) || !(v[1] == v[1])) done = 2;
+                else if (v[0] <= sc->tol2 * v[1]) done = 1;
+                sc->done = done;
+                *counter = 0u;
+            }
+        }
+    }
+};
+
+// The double-float march (the conduction tile of the one-problem kernel) with the register
+// budget of 3 resident blocks per SM.
+template <bool PER>
+__global__ void __launch_bounds__(NTHREADS, 3)
+residual_df_kernel(MarchGrid g, const Coef4<dfloat>* __restrict__ coef, LoadState<PolDF> ld, EpiResidualDF ep) {
+    ep.init();
+    const TileIdx t = decode_tile(g);
+    __shared__ TileSmem<PolDF, TX, TY> sm;
+    tc_tile<PolDF, TX, TY, LoadState<PolDF>, EpiResidualDF, PER>(g.c[0], t, coef, ld, ep, threadIdx.x + TX * threadIdx.y, sm);
+    ep.finish();
+}
+
+// double-float copies of the float64 Backward Euler records (4th word M = 1/w)
+__global__ void records_df_kernel(long long n, const Coef4<double>* rec, Coef4<dfloat>* out) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const Coef4<double> c = rec[t];
+        out[t] = Coef4<dfloat>{cvt<dfloat>(c.a), cvt<dfloat>(c.b), cvt<dfloat>(c.c), cvt<dfloat>(c.w)};
+    }
+}
 
 // r32 = rhs, d = 0, D^-1 = 1/(M - dt diag A) and the sums <r, D^-1 r>, <r, r>, <rhs, rhs>;
 // the last block initialises the scalar state of the inner solve.
@@ -63,6 +195,18 @@ __global__ void add_correction_kernel(long long n, double* x, const float* d) {
         x[t] += (double)d[t];
 }
 
+// The shadow's records from the context's current float64 ones: float32 records (w and M = 1/w
+// variants), float32 diag(A), and the double-float Backward Euler records.
+void refresh_shadow(Ctx& c, Ctx& s) {
+    s.dt_e = c.dt_e;
+    ops_f32()->store_coefs(s, c.coef64, static_cast<const double*>(c.adiag));
+    if (s.coef64) {
+        records_df_kernel<<<reduce_blocks(c), 256, 0, c.stream>>>(c.n, static_cast<const Coef4<double>*>(c.coef_be),
+                                                                  reinterpret_cast<Coef4<dfloat>*>(s.coef64));
+        PB_CUDA_TRY(cudaGetLastError());
+    }
+}
+
 void* dalloc(size_t bytes) {
     void* p = nullptr;
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
@@ -107,8 +251,10 @@ Ctx& mixed_shadow(Ctx& c) {
         s->d_pcg = static_cast<PcgScalars*>(dalloc(sizeof(PcgScalars)));
         PB_CUDA_TRY(cudaMemsetAsync(s->counter, 0, sizeof(unsigned int), c.stream));
         PB_CUDA_TRY(cudaMallocHost(&s->h_pcg, sizeof(PcgScalars)));
-        // float32 copies of the float64 records (w and M = 1/w variants) and of diag(A)
-        ops_f32()->store_coefs(*s, c.coef64, static_cast<const double*>(c.adiag));
+        // the shadow's float64-record slot holds the double-float Backward Euler records of the
+        // conduction residual (the same 32-byte stride)
+        if (c.kind == PB_TC_ANISO) s->coef64 = static_cast<Coef4<double>*>(dalloc(n * sizeof(Coef4<dfloat>)));
+        refresh_shadow(c, *s);
         PB_CUDA_TRY(cudaStreamSynchronize(c.stream));
     } catch (...) {
         free_shadow(s);
@@ -118,10 +264,33 @@ Ctx& mixed_shadow(Ctx& c) {
     return *s;
 }
 
+// Rewrites the shadow's records after every coefficient update (parabolic_update).
+void mixed_refresh(Ctx& c) {
+    if (c.shadow) refresh_shadow(c, *c.shadow);
+}
+
+// The outer residual of mixed-precision BE for conduction: r = b - S x (b = M u^n) into c.r
+// (float64) with <r, r>, <b, b> and the outer stopping decision in c.d_pcg, by the double-float
+// march over the double-float records.
+void mixed_residual(Ctx& c, const void* x, const void* un, double dt) {
+    Ctx& s = mixed_shadow(c);
+    if (!s.coef64) throw Error{PB_ENOTSUP, "the double-float residual is built for conduction"};
+    const Coef4<dfloat>* rec = reinterpret_cast<const Coef4<dfloat>*>(s.coef64);
+    EpiResidualDF ep{static_cast<const double*>(un), static_cast<const double*>(x), static_cast<double*>(c.r), dt,
+                     c.d_pcg, static_cast<double*>(c.partials), c.counter, c.grid.nblocks, {0.0, 0.0}};
+    const LoadState<PolDF> ld{static_cast<const double*>(x)};
+    KScope ks(c.prof, c.stream, K_PCG_INIT, (double)c.n * (8 + 8 + 32 + 8));
+    if (c.grid.c[0].periodic)
+        residual_df_kernel<true><<<c.grid.nblocks, dim3(TX, TY), 0, c.stream>>>(c.grid, rec, ld, ep);
+    else
+        residual_df_kernel<false><<<c.grid.nblocks, dim3(TX, TY), 0, c.stream>>>(c.grid, rec, ld, ep);
+    PB_CUDA_TRY(cudaGetLastError());
+}
+
 void free_shadow(Ctx* s) {
     if (!s) return;
     void* p[] = {s->coef, s->coef_be, s->adiag, s->r, s->p[0], s->p[1], s->q, s->dinv, s->y0, s->partials,
-                 s->counter, s->d_pcg};
+                 s->counter, s->d_pcg, s->coef64};
     for (void* q : p)
         if (q) cudaFree(q);
     if (s->h_pcg) cudaFreeHost(s->h_pcg);

@@ -389,6 +389,39 @@ def test_be_mixed_precision_refinement(kind):
     assert st["final_rel_residual"] <= 1e-10 and abs(st["cycles"] - log.cycles) <= 2
 
 
+def test_be_mixed_double_float_residual(monkeypatch):
+    """Mixed-precision BE on conduction drives its refinements with the double-float residual and
+    accepts a stop only on the float64 one: against float64 residuals throughout
+    (PB_MIXED_FP64_RESIDUAL=1) both runs meet the tolerance, take the oracle's PTL schedule within
+    the same slack, and differ by no more than their stopping tests allow."""
+    import paper_2403_01004_gb300 as pb
+    g, inp, op, u = tc_problem(32, 32, 64)
+    dt = 100.0 * op.dt_explicit()
+    _, log = be_advance(op, u, dt, use_ptl=True, rtol=1e-12)
+    res = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("PB_MIXED_FP64_RESIDUAL", flag)
+        ctx = gpu_ctx("tc", g, inp, "fp64")
+        ud = to_dev(u, ctx)
+        st = pb.be_pcg_advance(ctx, ud, dt, forced=log.dt_c, rtol=1e-10, mixed=True)
+        assert st["final_rel_residual"] <= 1e-10
+        res[flag] = (to_host(ud), st)
+        ctx.close()
+    (x64, s64), (xdf, sdf) = res["1"], res["0"]
+    assert sdf["cycles"] == s64["cycles"] == log.cycles
+    diff, bound = _be_state_bound(op, u, log.dt_c, xdf, x64, 1e-10, 1e-10)
+    assert diff <= bound, (diff, bound)
+    # the double-float run's last state passes the float64 test in the oracle too
+    ctx = gpu_ctx("tc", g, inp, "fp64")
+    ud = to_dev(u, ctx)
+    pb.be_pcg_advance(ctx, ud, dt, use_ptl=False, rtol=1e-10, mixed=True)
+    xo = to_host(ud)
+    b = u / op.w
+    r = b - (xo / op.w - dt * op.apply_A(xo))
+    assert np.linalg.norm(r) <= 1.001e-10 * np.linalg.norm(b)
+    ctx.close()
+
+
 @pytest.mark.parametrize("kind", ["tc", "visc"])
 def test_async_advance_replays_from_a_cuda_graph(kind):
     """rkl2_advance_async (a forced schedule, enqueued only) captured in a CUDA graph and replayed
