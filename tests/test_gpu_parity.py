@@ -423,6 +423,35 @@ def test_be_mixed_double_float_residual(monkeypatch):
 
 
 @pytest.mark.parametrize("kind", ["tc", "visc"])
+def test_be_mixed_after_coefficient_update(kind):
+    """parabolic_update also refreshes the float32 shadow (and the double-float records) of
+    mixed-precision BE: a context that solved with one operator and was then updated to another
+    solves exactly as a fresh context built on the second one (same iterations, same state)."""
+    import paper_2403_01004_gb300 as pb
+    import synth
+    from synth import device
+    shape = (32, 32, 64) if kind == "tc" else (24, 20, 16)
+    g, inp, op, u = tc_problem(*shape) if kind == "tc" else visc_problem(*shape)
+    inp2 = synth.tc_inputs(g, synth.SEED_BASE + 7, noise=0.05) if kind == "tc" else synth.visc_inputs(g, synth.SEED_BASE + 7)
+    fields2 = device.tc_fields(inp2) if kind == "tc" else device.visc_fields(inp2)
+    fresh = gpu_ctx(kind, g, inp2, "fp64")
+    dt = 100.0 * pb.parabolic_dt_explicit(fresh)
+    x_fresh = to_dev(u, fresh)
+    st_fresh = pb.be_pcg_advance(fresh, x_fresh, dt, use_ptl=False, rtol=1e-10, mixed=True)
+    upd = gpu_ctx(kind, g, inp, "fp64")
+    pb.be_pcg_advance(upd, to_dev(u, upd), 100.0 * pb.parabolic_dt_explicit(upd), use_ptl=False, rtol=1e-10,
+                      mixed=True)          # builds the shadow on the first operator
+    pb.parabolic_update(upd, fields2)
+    assert pb.parabolic_dt_explicit(upd) == pb.parabolic_dt_explicit(fresh)
+    x_upd = to_dev(u, upd)
+    st_upd = pb.be_pcg_advance(upd, x_upd, dt, use_ptl=False, rtol=1e-10, mixed=True)
+    assert st_upd["total_iters"] == st_fresh["total_iters"]
+    np.testing.assert_array_equal(to_host(x_upd), to_host(x_fresh))
+    fresh.close()
+    upd.close()
+
+
+@pytest.mark.parametrize("kind", ["tc", "visc"])
 def test_async_advance_replays_from_a_cuda_graph(kind):
     """rkl2_advance_async (a forced schedule, enqueued only) captured in a CUDA graph and replayed
     gives the synchronous call's result bit for bit; the PTL is refused by the graph-only form."""
