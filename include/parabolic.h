@@ -221,7 +221,11 @@ PB_API int rkl2_advance_async(pb_ctx* ctx, void* u_dev, double dt, const pb_adva
 /* Advances u (device, in place) over dt with Backward Euler, each cycle solving
  * (M - dt_c A) x = M u (M = diag(1/w), F = w A u) by point-Jacobi PCG from x0 = u, or from
  * x0_dev (device, ctx precision) on the first cycle when it is not NULL.  Supported for
- * PB_FP64 and PB_FP32 (float vectors, float64 dot products).  stats may be NULL. */
+ * PB_FP64 and PB_FP32 (float vectors, float64 dot products).  stats may be NULL.
+ * With opts->mixed_precision on a PB_FP64 conduction context the outer residuals that drive
+ * the refinements are computed in double-float arithmetic (about 48 bits, on the float32
+ * pipes), and a cycle stops only when the float64 residual meets rtol; environment
+ * PB_MIXED_FP64_RESIDUAL=1 (read at each call) uses float64 residuals throughout. */
 PB_API int be_pcg_advance(pb_ctx* ctx, void* u_dev, double dt, const pb_advance_opts* opts,
                    const void* x0_dev, pb_stats* stats);
 
