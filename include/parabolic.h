@@ -61,11 +61,16 @@ extern "C" {
 #define PB_ETIMEOUT      7  /* a bounded device-side wait ran out                           */
 #define PB_ENOTSUP       8  /* combination not supported by this build                      */
 
-/* PB_FP64: float64 states, records and arithmetic.  PB_FP32: float32 throughout (reductions and
- * coefficients in float64).  PB_BF16_STORE: bfloat16 states, float32 records and arithmetic.
- * PB_FP64_STORE: float64 states and stage recurrence, float32 records and stencil arithmetic --
- * the storage rounding that accumulates over the stages of a long cycle is that of float64,
- * while the stencil runs at float32 rates (STS only; BE + PCG needs PB_FP64 or PB_FP32). */
+/* PB_FP64: float64 states, records and arithmetic.  PB_FP32: float32 states, records and
+ * stencil arithmetic; the super-time-stepping stage recurrence is summed in double-float
+ * arithmetic on the float32 pipes (float64 coefficients as float pairs), so a stage adds only
+ * the rounding of its stored result; reductions and coefficients in float64.
+ * PB_BF16_STORE: bfloat16 storage with float32 accumulation -- the caller's state arrays and
+ * the operator's coefficient records are bfloat16; within a call the state and the stage values
+ * are float32 (a context-owned working copy), with the PB_FP32 stage recurrence; the state is
+ * rounded to bfloat16 once, when the call hands it back (STS, apply and PTL only).
+ * PB_FP64_STORE: float64 states and stage recurrence, float32 records and stencil arithmetic
+ * (STS only; BE + PCG needs PB_FP64 or PB_FP32). */
 typedef enum { PB_FP64 = 0, PB_FP32 = 1, PB_BF16_STORE = 2, PB_FP64_STORE = 3 } pb_precision;
 typedef enum { PB_TC_ANISO = 0, PB_VISC_ISO = 1 } pb_op_kind;
 typedef enum { PB_RKL2 = 0, PB_RKG2 = 1 } pb_scheme;
@@ -167,8 +172,9 @@ PB_API const char* pb_last_error(const pb_ctx* ctx);
 /* Builds a context: validates the grid, allocates its device workspace (owned by the context),
  * computes the frozen operator coefficients in float64 on the device (lagged kappa, Sec. 2) and
  * stores them in the context precision, and reduces dt_E.  precision: PB_FP64, PB_FP32 (float
- * state and arithmetic; PTL and PCG reductions in float64), PB_BF16_STORE (bfloat16 state,
- * float coefficients and arithmetic) or PB_FP64_STORE (see pb_precision).  cuda_stream is a cudaStream_t (NULL = legacy default). */
+ * state and arithmetic; PTL and PCG reductions in float64), PB_BF16_STORE (bfloat16 state and
+ * records, float32 working state and arithmetic) or PB_FP64_STORE (see pb_precision).
+ * cuda_stream is a cudaStream_t (NULL = legacy default). */
 PB_API int parabolic_setup(const pb_grid* grid, const pb_operator* op, int32_t precision,
                     void* cuda_stream, pb_ctx** out);
 
@@ -181,7 +187,8 @@ PB_API int parabolic_update(pb_ctx* ctx, const pb_operator* op);
 /* Frees the context and its device workspace.  NULL is accepted. */
 PB_API int parabolic_destroy(pb_ctx* ctx);
 
-/* Length of the state vector (elements) and the element size in bytes (8, 4 or 2). */
+/* Length of the state vector (elements) and the element size in bytes of the caller's state
+ * arrays (8, 4 or 2). */
 PB_API int parabolic_state_size(const pb_ctx* ctx, int64_t* n_elems, int32_t* elem_bytes);
 
 /* The explicit (forward Euler) stable step dt_E of the operator (Appendix A's Delta t_Euler). */
@@ -344,20 +351,24 @@ PB_API int learned_guess(pb_ctx* ctx, pb_model* model, const void* u, double dt,
  * no cudaFree, no allocating library call): the caller passes
  *   records  the operator's packed per-point records, n Coef4 entries in the layout the library
  *            uses (conduction: {ahat_r, ahat_t, ahat_p} of corner [i,j,k] and the cell weight w;
- *            viscosity: {c_r, c_t, c_p} of the +1 faces and w), float64 for PB_FP64, float32 for
- *            PB_FP32 and PB_BF16_STORE;
- *   u        the state (n elements of the precision's storage type), read only;
+ *            viscosity: {c_r, c_t, c_p} of the +1 faces and w), 4 words of the type below;
+ *   u        the state (n elements, type below), read only;
  *   F        output, n elements: F = L u;
  * and receives dt_ptl, k_index and fmax on the host (any may be NULL).  n is n_r*n_theta*n_phi
- * for conduction and the three-component total for viscosity.  The paper has no counterpart:
- * this is a deployment variant of the PTL pass.
+ * for conduction and the three-component total for viscosity.  Types per precision:
+ *   PB_FP64        records, u and F float64;
+ *   PB_FP32        records, u and F float32;
+ *   PB_BF16_STORE  records and u bfloat16, F float32 (the precision's working type).
+ * The paper has no counterpart: this is a deployment variant of the PTL pass.
  * Its only scratch (per-block partials, a flag, the result) is one file-scope device array of
  * 1 MiB that every GPU loading the library holds until exit; grids needing more than 65,520
  * partial records (more than that many 32 x 8 (r, theta) tiles) are rejected with PB_EINVAL.
- * The first call on a device looks up that array's device address (cudaGetSymbolAddress); make
- * it before any stream capture.  Every call shares the array, so calls whose work overlaps on
- * the GPU (other streams, other host threads) race; serialise them.  Work runs on `stream`
- * (cudaStream_t, NULL = legacy default) and the call returns after it completes.
+ * The first call in a device's context looks up that array's device address
+ * (cudaGetSymbolAddress) and later calls reuse it; after a device reset (a new context) it is
+ * looked up again.  Every call shares the array, so calls whose work overlaps on the GPU (other
+ * streams, other host threads) race; serialise them.  Work runs on `stream` (cudaStream_t,
+ * NULL = legacy default) and the call waits for its own result (a copy to host memory and a
+ * stream synchronisation), so it can never be made inside a stream capture.
  * Returns PB_OK, PB_EINVAL, PB_ENONFINITE (non-finite F) or PB_ECUDA. */
 PB_API int pb_ptl_noalloc(int32_t kind, int32_t n_r, int32_t n_theta, int32_t n_phi,
                           int32_t precision, const void* records, const void* u, void* F,

@@ -88,7 +88,7 @@ void free_ctx(Ctx& c) {
     c.shadow = nullptr;
     void* ptrs[] = {c.coef, c.coef_be, c.coef64, c.adiag, c.y0, c.buf[0], c.buf[1], c.buf[2], c.r, c.p[0],
                     c.p[1], c.q, c.dinv, c.partials, c.counter, c.d_pcg, c.d_scalar, c.d_flag, c.d_err,
-                    c.spec};
+                    c.spec, c.work};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c.s64) cudaFree(c.s64);
@@ -103,7 +103,7 @@ void free_ctx(Ctx& c) {
 
 // Second state buffer for speculated cycles, and the event the host waits on for a PTL result.
 void* ensure_spec(Ctx& c) {
-    if (!c.spec) c.spec = dmalloc((size_t)c.n * c.elem);
+    if (!c.spec) c.spec = dmalloc((size_t)c.n * c.welem);
     return c.spec;
 }
 
@@ -339,18 +339,20 @@ int parabolic_setup(const pb_grid* g, const pb_operator* op, int32_t precision, 
             c.kind = op->kind;
             c.prec = precision;
             c.elem = (precision == PB_FP64 || precision == PB_FP64_STORE) ? 8 : precision == PB_FP32 ? 4 : 2;
+            c.welem = (precision == PB_FP64 || precision == PB_FP64_STORE) ? 8 : 4;
             c.stream = static_cast<cudaStream_t>(stream);
             c.nr = g->n_r; c.nt = g->n_theta; c.np = g->n_phi;
             c.geometry = g->geometry;
             PB_CUDA_TRY(cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, dev));
             build_grid(c);
-            const size_t csz = precision == PB_FP64 ? 8 : 4;
+            const size_t csz = precision == PB_FP64 ? 8 : precision == PB_BF16_STORE ? 2 : 4;
             c.coef = dmalloc((size_t)c.n * 4 * csz);
             c.coef_be = dmalloc((size_t)c.n * 4 * csz);
             c.coef64 = static_cast<Coef4<double>*>(dmalloc((size_t)c.n * sizeof(Coef4<double>)));
             c.adiag = dmalloc((size_t)c.n * csz);
-            c.y0 = dmalloc((size_t)c.n * c.elem);
-            for (int b = 0; b < 3; ++b) c.buf[b] = dmalloc((size_t)c.n * c.elem);
+            c.y0 = dmalloc((size_t)c.n * c.welem);
+            for (int b = 0; b < 3; ++b) c.buf[b] = dmalloc((size_t)c.n * c.welem);
+            if (c.welem != c.elem) c.work = dmalloc((size_t)c.n * c.welem);
             c.partial_cap = std::max(c.grid.nblocks, 3 * reduce_blocks(c)) + 32;
             c.partials = dmalloc((size_t)c.partial_cap * 32);
             c.counter = static_cast<unsigned int*>(dmalloc(sizeof(unsigned int)));
@@ -456,7 +458,14 @@ int parabolic_apply(pb_ctx* h, const void* u, void* F) {
     return guarded(&c, [&] {
         if (!u || !F) throw Error{PB_EINVAL, "null state pointer"};
         if (u == F) throw Error{PB_EINVAL, "u and F must not alias"};
-        ops_of(c)->apply(c, u, F);
+        Ops* ops = ops_of(c);
+        const void* wu = ops->enter(c, u);
+        if (wu == u) {
+            ops->apply(c, u, F);
+        } else {           // bfloat16 storage: F in float32, then into the caller's bfloat16 array
+            ops->apply(c, wu, c.y0);
+            ops->leave(c, c.y0, F);
+        }
         sync(c);
     });
 }
@@ -466,7 +475,8 @@ int ptl_compute(pb_ctx* h, const void* u, double* dt_ptl, int64_t* k, double* fm
     Ctx& c = h->c;
     return guarded(&c, [&] {
         if (!u) throw Error{PB_EINVAL, "null state pointer"};
-        const PtlResult r = run_ptl(c, ops_of(c), u);
+        Ops* ops = ops_of(c);
+        const PtlResult r = run_ptl(c, ops, ops->enter(c, u));
         if (r.nonfinite) throw Error{PB_ENONFINITE, "non-finite F in the PTL pass"};
         if (dt_ptl) *dt_ptl = r.dt_ptl;
         if (k) *k = r.k;
@@ -479,7 +489,8 @@ int ptl_full_compute(pb_ctx* h, const void* u, double* dt_full, int64_t* cell, i
     Ctx& c = h->c;
     return guarded(&c, [&] {
         if (!u) throw Error{PB_EINVAL, "null state pointer"};
-        const PtlResult r = run_ptl(c, ops_of(c), u, true);
+        Ops* ops = ops_of(c);
+        const PtlResult r = run_ptl(c, ops, ops->enter(c, u), true);
         if (r.nonfinite) throw Error{PB_ENONFINITE, "non-finite F in the PTL pass"};
         if (dt_full) *dt_full = r.dt_full;
         if (cell) *cell = r.key_full >= 0 ? r.key_full / 3 : -1;
@@ -499,15 +510,20 @@ int rkl2_advance_async(pb_ctx* h, void* u, double dt, const pb_advance_opts* opt
             throw Error{PB_EINVAL, "the PTL needs a host round trip per cycle: use rkl2_advance, or a forced schedule"};
         Ops* ops = ops_of(c);
         const int n = forced ? o.n_forced : 1;
-        Sts co;
         for (int cycle = 0; cycle < n; ++cycle) {
             const double dt_c = forced ? o.dt_cycles[cycle] : dt;
             if (!(dt_c >= 0.0) || std::isinf(dt_c)) throw Error{PB_EINVAL, "cycle length must be finite and >= 0"};
+        }
+        void* wu = ops->enter(c, u);     // the caller's array, or the float32 working copy
+        Sts co;
+        for (int cycle = 0; cycle < n; ++cycle) {
+            const double dt_c = forced ? o.dt_cycles[cycle] : dt;
             if (dt_c == 0.0) continue;
             make_sts(o.scheme, dt_c / c.dt_e, co);
-            ops->apply(c, u, c.y0);
-            enqueue_stages(c, ops, co, dt_c, u, u);
+            ops->apply(c, wu, c.y0);
+            enqueue_stages(c, ops, co, dt_c, wu, wu);
         }
+        if (wu != u) ops->leave(c, wu, u);
     });
 }
 
@@ -522,6 +538,9 @@ int rkl2_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, pb_
         if (!u) throw Error{PB_EINVAL, "null state pointer"};
         if (!(dt >= 0.0) || std::isinf(dt)) throw Error{PB_EINVAL, "dt must be finite and >= 0"};
         Ops* ops = ops_of(c);
+        // the working state: u itself, or the float32 copy of a bfloat16-storage context's state
+        void* const wu = ops->enter(c, u);
+        cur = wu;
         const bool forced = o.n_forced > 0;
         const bool want_full = o.ptl_mode == PB_PTL_FULL || (st && st->dt_full_cycle);
         const double floor_dt = o.ptl_floor * c.dt_e;
@@ -574,7 +593,7 @@ int rkl2_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, pb_
                 ops->ptl_finalize(c, cur, c.y0);
                 if (want_full) ops->ptl_full(c, cur, c.y0);
                 PB_CUDA_TRY(cudaEventRecord(c.ev_ptl, c.stream));
-                void* nxt = cur == u ? ensure_spec(c) : u;
+                void* nxt = cur == wu ? ensure_spec(c) : wu;
                 stages(dt_c, cur, nxt);
                 PB_CUDA_TRY(cudaEventSynchronize(c.ev_ptl));
                 const PtlResult r = *c.h_ptl;
@@ -596,14 +615,17 @@ int rkl2_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, pb_
             }
         }
         if (cur != u) {
-            PB_CUDA_TRY(cudaMemcpyAsync(u, cur, (size_t)c.n * c.elem, cudaMemcpyDeviceToDevice, c.stream));
+            ops->leave(c, cur, u);
             cur = u;
         }
         sync(c);
     });
     if (rc != PB_OK && cur != u) {
-        // the last completed cycle lives in the speculation buffer: hand it back
-        cudaMemcpyAsync(u, cur, (size_t)c.n * c.elem, cudaMemcpyDeviceToDevice, c.stream);
+        // the last completed cycle lives in the speculation buffer or the working copy: hand it back
+        try {
+            ops_of(c)->leave(c, cur, u);
+        } catch (const Error&) {
+        }
         cudaStreamSynchronize(c.stream);
     }
     if (rc != PB_OK && st) st->status_cycle = cycle;

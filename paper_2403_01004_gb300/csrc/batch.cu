@@ -37,8 +37,14 @@ struct BatchProblem {
 
 struct BatchSeg { long long begin; int p; int level; };
 
-// level-2 record: {a1, cy, cf, -}; level L >= 3 record: {mu, nu, mdt, ydt}
-struct LevelCoef { float a, b, c, d; };
+// level-2 record: {a1, cy, cf, -}; level L >= 3 record: {mu, nu, mdt, ydt}; each float64
+// coefficient as a float pair (the double-float stage recurrence of the float32 policy)
+struct LevelCoef { float a, b, c, d, al, bl, cl, dl; };
+
+static LevelCoef level_coef(double a, double b, double c, double d) {
+    auto lo = [](double x) { return (float)(x - (double)(float)x); };
+    return LevelCoef{(float)a, (float)b, (float)c, (float)d, lo(a), lo(b), lo(c), lo(d)};
+}
 
 namespace {
 
@@ -77,10 +83,10 @@ __device__ void run_item(const BatchProblem& pr, int L, int t, const LevelCoef* 
     } else if (L == 2) {
         const LevelCoef c = lc[pr.coef_off + 2];
         if (last) {
-            EpiStage2<P, true> ep{pr.u, nullptr, pr.u, c.a, c.b, c.c};
+            EpiStage2<P, true> ep{pr.u, nullptr, pr.u, c.a, c.b, c.c, nullptr, c.al, c.bl, c.cl};
             tc_tile<P, TXv, TYv>(pr.cg, ti, pr.coef, LoadState<P>{pr.y0}, ep, tid, sm);
         } else {
-            EpiStage2<P, false> ep{nullptr, pr.buf[0], pr.buf[1], c.a, c.b, c.c};
+            EpiStage2<P, false> ep{nullptr, pr.buf[0], pr.buf[1], c.a, c.b, c.c, nullptr, c.al, c.bl, c.cl};
             tc_tile<P, TXv, TYv>(pr.cg, ti, pr.coef, LoadState<P>{pr.y0}, ep, tid, sm);
         }
     } else {
@@ -88,10 +94,11 @@ __device__ void run_item(const BatchProblem& pr, int L, int t, const LevelCoef* 
         const float* dkm1 = pr.buf[(L - 2) % 3];
         const float* dkm2 = pr.buf[(L - 3) % 3];
         if (last) {
-            EpiStage<P, true, true> ep{dkm2, pr.y0, pr.u, pr.u, c.a, c.b, c.c, c.d};
+            EpiStage<P, true, true> ep{dkm2, pr.y0, pr.u, pr.u, c.a, c.b, c.c, c.d, nullptr, c.al, c.bl, c.cl, c.dl};
             tc_tile<P, TXv, TYv>(pr.cg, ti, pr.coef, LoadState<P>{dkm1}, ep, tid, sm);
         } else {
-            EpiStage<P, true, false> ep{dkm2, pr.y0, nullptr, pr.buf[(L - 1) % 3], c.a, c.b, c.c, c.d};
+            EpiStage<P, true, false> ep{dkm2, pr.y0, nullptr, pr.buf[(L - 1) % 3], c.a, c.b, c.c, c.d, nullptr, c.al, c.bl,
+                                        c.cl, c.dl};
             tc_tile<P, TXv, TYv>(pr.cg, ti, pr.coef, LoadState<P>{dkm1}, ep, tid, sm);
         }
     }
@@ -298,11 +305,10 @@ std::vector<long long> build_tables(pb_batch* b, void* const* u, const double* d
         const double dt = dts[p];
         const double a1 = mut[1] * dt;
         LevelCoef* L = b->h_lc + lc_off;
-        L[0] = L[1] = LevelCoef{0, 0, 0, 0};
+        L[0] = L[1] = level_coef(0, 0, 0, 0);
         const double ydt2 = (mut[2] + gt[2]) * dt;
-        L[2] = LevelCoef{(float)a1, (float)(mu[2] * a1 + ydt2), (float)(mut[2] * dt * a1), 0.f};
-        for (int k = 3; k <= pr.s; ++k)
-            L[k] = LevelCoef{(float)mu[k], (float)nu[k], (float)(mut[k] * dt), (float)((mut[k] + gt[k]) * dt)};
+        L[2] = level_coef(a1, mu[2] * a1 + ydt2, mut[2] * dt * a1, 0.0);
+        for (int k = 3; k <= pr.s; ++k) L[k] = level_coef(mu[k], nu[k], mut[k] * dt, (mut[k] + gt[k]) * dt);
         lc_off += pr.s + 1;
         done_off += pr.s + 1;
         key.push_back(pr.s);

@@ -15,17 +15,26 @@
 namespace pb {
 
 // ---- precision policies -----------------------------------------------------------------
-// S: state storage, C: coefficient storage, A: stencil / stage arithmetic.
+// S: storage of the working state and the stage values (y0, the stage increments); C: coefficient
+// records; A: stencil arithmetic; E: the stage recurrence (the update of the stored stage values
+// from A-precision F); U: the caller's state arrays (S, or bfloat16 held in a float32 working
+// copy during a call).  DF: the float32 stage recurrence runs in double-float arithmetic (see
+// DfAcc), so the only rounding a stage adds is the store of its result.
 // CG: operands may have been written earlier in the same launch (the batched persistent kernel),
 // so they are read through L2 (ld.global.cg) instead of the non-coherent read-only path.
-// S: storage of states and stage values; C: coefficient records; A: stencil arithmetic;
-// E: the stage recurrence (the update of the stored stage values from A-precision F).
-struct PolF64 { using S = double; using C = double; using A = double; using E = double; static constexpr int id = PB_FP64; static constexpr bool CG = false; };
-struct PolF32 { using S = float; using C = float; using A = float; using E = float; static constexpr int id = PB_FP32; static constexpr bool CG = false; };
-struct PolB16 { using S = __nv_bfloat16; using C = float; using A = float; using E = float; static constexpr int id = PB_BF16_STORE; static constexpr bool CG = false; };
+struct PolF64 { using S = double; using C = double; using A = double; using E = double; using U = double;
+                static constexpr int id = PB_FP64; static constexpr bool CG = false; static constexpr bool DF = false; };
+struct PolF32 { using S = float; using C = float; using A = float; using E = float; using U = float;
+                static constexpr int id = PB_FP32; static constexpr bool CG = false; static constexpr bool DF = true; };
+// bfloat16 storage with float32 accumulation: the operator records (the largest stream of every
+// pass) and the caller's state are bfloat16; the stage values and the state between the cycles
+// of a call are float32, where rounding would otherwise accumulate over the stages
+struct PolB16 { using S = float; using C = __nv_bfloat16; using A = float; using E = float; using U = __nv_bfloat16;
+                static constexpr int id = PB_BF16_STORE; static constexpr bool CG = false; static constexpr bool DF = true; };
 // float64 storage and recurrence, float32 records and stencil (GB300: float64 arithmetic is
 // scarce, bandwidth is not; the stage recurrence is where storage rounding accumulates)
-struct PolF64S { using S = double; using C = float; using A = float; using E = double; static constexpr int id = PB_FP64_STORE; static constexpr bool CG = false; };
+struct PolF64S { using S = double; using C = float; using A = float; using E = double; using U = double;
+                 static constexpr int id = PB_FP64_STORE; static constexpr bool CG = false; static constexpr bool DF = false; };
 struct PolF32CG : PolF32 { static constexpr bool CG = true; };
 
 template <typename T> __host__ __device__ __forceinline__ float to_f(T v);
@@ -66,6 +75,18 @@ template <> __device__ __forceinline__ Coef4<float> load_coef<float, float>(cons
     float4 x = __ldg(reinterpret_cast<const float4*>(p));
     return Coef4<float>{x.x, x.y, x.z, x.w};
 }
+// bfloat16 record: one 8-byte load; a bfloat16 is the upper half of the float with the same value
+template <> __device__ __forceinline__ Coef4<float> load_coef<float, __nv_bfloat16>(const Coef4<__nv_bfloat16>* p) {
+    const uint2 x = __ldg(reinterpret_cast<const uint2*>(p));
+    return Coef4<float>{__uint_as_float(x.x << 16), __uint_as_float(x.x & 0xffff0000u), __uint_as_float(x.y << 16),
+                        __uint_as_float(x.y & 0xffff0000u)};
+}
+// One word of a record (a neighbour's face coefficient)
+template <typename A, typename C> __device__ __forceinline__ A coef_word(const C* p) { return cvt<A>(ldg(p)); }
+
+// float64 set-up value into the record precision (one rounding)
+template <typename C> __device__ __forceinline__ C to_rec(double v) { return (C)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 to_rec<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
 
 // ---- grid descriptors ----------------------------------------------------------------------
 // Stencil tiles: TX cells along r (a full warp, coalesced) x TY cells along theta; each block
@@ -124,8 +145,10 @@ struct Ctx {
     void* coef_be = nullptr;       // Coef4<C>[n], 4th word M = 1/w (Backward Euler system)
     Coef4<double>* coef64 = nullptr;  // float64 record (kept for refinement / diagnostics)
     void* adiag = nullptr;         // diag(A) in C precision [n]
-    void* y0 = nullptr;            // state-typed scratch [n]
+    int welem = 8;                 // element size of the working state and stage values (sizeof S)
+    void* y0 = nullptr;            // working-precision scratch [n]
     void* buf[3] = {nullptr, nullptr, nullptr};
+    void* work = nullptr;          // float32 working state of a bfloat16-storage context [n]
     // PCG vectors (S precision)
     void* r = nullptr; void* p[2] = {nullptr, nullptr}; void* q = nullptr; void* dinv = nullptr;
     // reductions
@@ -148,7 +171,7 @@ struct Ctx {
     double* geo[16] = {};          // device copies of the face / point coordinate arrays
     Prof prof;
     struct Ctx* shadow = nullptr;  // float32 shadow for mixed-precision BE (float64 contexts)
-    void* spec = nullptr;          // second state buffer of speculated floor cycles [n]
+    void* spec = nullptr;          // second working-state buffer of speculated floor cycles [n]
     cudaEvent_t ev_ptl = nullptr;  // recorded after a PTL result's copy to the host
     std::string err;
     int sm_count = 0;

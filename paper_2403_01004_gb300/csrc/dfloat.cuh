@@ -1,0 +1,82 @@
+// Double-float arithmetic on the float32 pipes: the accurate sums and products of a value held
+// as two floats, and the stage-recurrence helper of the float32 and bfloat16-storage policies.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace pb {
+
+// A value held as the unevaluated sum hi + lo of two floats (|lo| <= ulp(hi) / 2), about 48
+// significant bits, computed on the float32 pipes (GB300 issues float64 at a small fraction of
+// the float32 rate).  Sums follow Knuth's two-sum and Dekker's fast two-sum (the accurate
+// double-float addition); products take the exact rounding error of hi * hi from a fused
+// multiply-add.  Every operation is an explicit round-to-nearest intrinsic, so the compiler
+// neither contracts nor reorders the error terms.
+struct dfloat {
+    float hi, lo;
+    dfloat() = default;
+    __device__ constexpr dfloat(float h) : hi(h), lo(0.f) {}
+    __device__ constexpr dfloat(float h, float l) : hi(h), lo(l) {}
+};
+
+__device__ __forceinline__ dfloat two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return dfloat(s, e);
+}
+__device__ __forceinline__ dfloat fast_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return dfloat(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ dfloat operator+(dfloat x, dfloat y) {
+    dfloat s = two_sum(x.hi, y.hi);
+    const dfloat t = two_sum(x.lo, y.lo);
+    s = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ dfloat operator-(dfloat x) { return dfloat(-x.hi, -x.lo); }
+__device__ __forceinline__ dfloat operator-(dfloat x, dfloat y) { return x + (-y); }
+__device__ __forceinline__ dfloat operator*(dfloat x, dfloat y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ double to_double(dfloat x) { return (double)x.hi + (double)x.lo; }
+
+// Running sum of products c_i v_i with float64 coefficients c_i = hi_i + lo_i (split on the host)
+// and float operands v_i, in double-float: each product's rounding error comes from a fused
+// multiply-add, the leading parts are added by two-sum and every error term is gathered in e.
+// The value s + e carries about 44 significant bits of the terms' magnitude, so the stage
+// recurrence loses nothing to its own arithmetic (or to the float rounding of its coefficients);
+// only the store of the result rounds.
+struct DfAcc {
+    float s = 0.f, e = 0.f;
+    __device__ __forceinline__ void add(float ch, float cl, float v) {
+        const float p = __fmul_rn(ch, v);
+        float err = __fmaf_rn(ch, v, -p);
+        err = __fmaf_rn(cl, v, err);
+        const dfloat t = two_sum(s, p);
+        s = t.hi;
+        e = __fadd_rn(e, __fadd_rn(t.lo, err));
+    }
+    // add a float value exactly (the state u_0 of the last stage)
+    __device__ __forceinline__ void add(float v) {
+        const dfloat t = two_sum(s, v);
+        s = t.hi;
+        e = __fadd_rn(e, t.lo);
+    }
+    __device__ __forceinline__ float value() const { return __fadd_rn(s, e); }
+};
+
+// c v rounded once, with c = hi + lo
+__device__ __forceinline__ float df_scale(float ch, float cl, float v) {
+    const float p = __fmul_rn(ch, v);
+    float err = __fmaf_rn(ch, v, -p);
+    err = __fmaf_rn(cl, v, err);
+    return __fadd_rn(p, err);
+}
+
+}  // namespace pb

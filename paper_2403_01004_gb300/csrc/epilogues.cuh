@@ -5,6 +5,7 @@
 #include <climits>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "march.cuh"
 #include "reduce.cuh"
 
@@ -13,6 +14,14 @@ namespace pb {
 struct NoPre {};
 
 // ---- loaders -------------------------------------------------------------------------------
+// A state stored in type T (the caller's bfloat16 array of a bfloat16-storage policy)
+template <class P, typename T>
+struct LoadStateT {
+    const T* u;
+    __device__ void init() {}
+    __device__ typename P::A operator()(long long idx) const { return cvt<typename P::A>(ldg(u + idx)); }
+};
+
 template <class P>
 struct LoadState {
     const typename P::S* u;
@@ -75,6 +84,7 @@ struct EpiF {
     // point, non-finite values win it and are reported once at the end
     K bk;
     long long bi;
+    float al = 0.f;                  // low part of a (double-float policies)
     static constexpr int NC = 0;     // point operands delivered by the TMA kernel
     __device__ void init() { bk = K(-1); bi = LLONG_MAX; }
     __device__ bool skip() const { return false; }
@@ -85,7 +95,10 @@ struct EpiF {
         const A f = w * Au;
         const S fs = cvt<S>(f);
         F[idx] = fs;
-        if (U1) u1[idx] = cvt<S>(a * f);
+        if constexpr (U1) {
+            if constexpr (P::DF) u1[idx] = cvt<S>(df_scale(a, al, f));
+            else u1[idx] = cvt<S>(a * f);
+        }
         if (ARGMAX) {
             const K key = MagKey<A>::of(fabs(cvt<A>(fs)));
             if (key > bk) { bk = key; bi = idx; }    // a thread visits its indices in rising order
@@ -109,7 +122,10 @@ struct EpiF {
 // + mut dt F(u_{k-1}) + gt dt y_0; it drops the u_0 read from every stage but the last and
 // keeps stored stage values small (the rounding of reduced-precision storage acts on d, not u).
 // The last stage writes u_s = u_0 + d_s over u_0 in place (each point is read before it is
-// written, by the same thread).
+// written, by the same thread).  Under a double-float policy (P::DF) the right-hand side, u_0
+// included, is summed in double-float with the float64 coefficients split into float pairs, so
+// the stage adds one rounding, the store's (float32 arithmetic would add several, at the
+// magnitude of the largest term: in the stiff modes mdt F and ydt y_0 nearly cancel).
 template <class P, bool KM2, bool LAST>
 struct EpiStage {
     using A = typename P::A;
@@ -125,6 +141,7 @@ struct EpiStage {
     S* out;
     E mu, nu, mdt, ydt;
     const S* dkm1;
+    float mul = 0.f, nul = 0.f, mdtl = 0.f, ydtl = 0.f;   // low parts of the coefficients (P::DF)
     // point operands of the TMA kernel, in this order: y0, d_{k-2} (KM2), u0 (LAST)
     static constexpr int NC = 1 + (KM2 ? 1 : 0) + (LAST ? 1 : 0);
     __device__ void apply_c(long long idx, A Au, A w, E d1, E c0, E c1, E c2) {
@@ -140,8 +157,18 @@ struct EpiStage {
         update(idx, Au, w, kExact ? p.dkm1 : (E)d1, p.dkm2, p.y0, p.u0);
     }
     __device__ void update(long long idx, A Au, A w, E d1, E d2, E y, E u) {
-        const E d = mu * d1 + nu * d2 + mdt * (E)(w * Au) + ydt * y;
-        out[idx] = cvt<S>(LAST ? u + d : d);
+        if constexpr (P::DF) {
+            DfAcc acc;
+            acc.add(mu, mul, d1);
+            if (KM2) acc.add(nu, nul, d2);
+            acc.add(mdt, mdtl, __fmul_rn(w, Au));
+            acc.add(ydt, ydtl, y);
+            if (LAST) acc.add(u);
+            out[idx] = cvt<S>(acc.value());
+        } else {
+            const E d = mu * d1 + nu * d2 + mdt * (E)(w * Au) + ydt * y;
+            out[idx] = cvt<S>(LAST ? u + d : d);
+        }
     }
     __device__ void finish() {}
 };
@@ -163,6 +190,7 @@ struct EpiStage2 {
     S* out;
     E a, cy, cf;       // a = mut_1 dt, cy = mu_2 a + ydt, cf = mdt a
     const S* y0;       // the marched field, reloaded exactly when E is wider than A
+    float al = 0.f, cyl = 0.f, cfl = 0.f;   // low parts of the coefficients (P::DF)
     static constexpr int NC = LAST ? 1 : 0;
     __device__ void init() {}
     __device__ bool skip() const { return false; }
@@ -172,12 +200,24 @@ struct EpiStage2 {
     __device__ void apply_c(long long idx, A Au, A w, E y, E c0, E, E) { update(idx, Au, w, y, c0); }
     __device__ void apply(long long idx, A Au, A w, A y, const Pre& p) { update(idx, Au, w, kExact ? p.y : (E)y, p.u0); }
     __device__ void update(long long idx, A Au, A w, E y, E u) {
-        const E d2 = cy * y + cf * (E)(w * Au);
-        if (LAST) {
-            out[idx] = cvt<S>(u + d2);
+        if constexpr (P::DF) {
+            DfAcc acc;
+            acc.add(cy, cyl, y);
+            acc.add(cf, cfl, __fmul_rn(w, Au));
+            if (LAST) {
+                acc.add(u);
+            } else {
+                d1[idx] = cvt<S>(df_scale(a, al, y));
+            }
+            out[idx] = cvt<S>(acc.value());
         } else {
-            d1[idx] = cvt<S>(a * y);
-            out[idx] = cvt<S>(d2);
+            const E d2 = cy * y + cf * (E)(w * Au);
+            if (LAST) {
+                out[idx] = cvt<S>(u + d2);
+            } else {
+                d1[idx] = cvt<S>(a * y);
+                out[idx] = cvt<S>(d2);
+            }
         }
     }
     __device__ void finish() {}
@@ -403,9 +443,9 @@ pcg_update_f32x4_kernel(long long n, float* x, float* r, const float* p, const f
 // (a march launch leaves thousands of partials: more threads shorten each one's chain of loads).
 constexpr int kFinalizeThreads = 1024;
 
-template <class P>
+template <class P, typename UT = typename P::S>
 __global__ void __launch_bounds__(kFinalizeThreads)
-ptl_finalize_kernel(MarchGrid g, const typename P::S* u, const typename P::S* F,
+ptl_finalize_kernel(MarchGrid g, const UT* u, const typename P::S* F,
                     const ArgMax* part, int nparts, PtlResult* res, const int* nonfinite) {
     using A = typename P::A;
     double v = -1.0;

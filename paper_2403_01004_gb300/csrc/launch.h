@@ -33,6 +33,12 @@ public:
     // PCG: set-up from x (in place) and u^n; one SpMV + update iteration
     virtual void pcg_init(Ctx& c, const void* x, const void* un, double dt) = 0;
     virtual void pcg_iter(Ctx& c, void* x, int parity, double dt) = 0;
+    // The state the kernels work on: the caller's array itself, or, under bfloat16 storage, the
+    // context's float32 working copy (c.work) filled from it
+    virtual void* enter(Ctx& c, const void* u) = 0;
+    // Hands a working state back to the caller's array u (a conversion under bfloat16 storage,
+    // otherwise a copy when the two differ)
+    virtual void leave(Ctx& c, const void* work, void* u) = 0;
     // converts the float64 coefficient records into the context's storage precision
     virtual void store_coefs(Ctx& c, const Coef4<double>* rec, const double* adiag) = 0;
     virtual bool supports_pcg() const = 0;

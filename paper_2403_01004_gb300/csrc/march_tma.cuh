@@ -99,7 +99,14 @@ struct TmaLayout {
     static constexpr int U_BYTES = (TY + 2) * BXW * (int)sizeof(S);
     static constexpr int U_PITCH = align128(U_BYTES);
     static constexpr int F_BYTES = (TY + 2) * BXW * (int)sizeof(typename Field::FT);
-    static constexpr int C_BYTES = (TY + 1) * (TX + 1) * 4 * (int)sizeof(C);
+    // records: a 4-D box of 4 words x (TX + 1) x (TY + 1) corners; bfloat16 records (8 bytes, a
+    // 4-word row of 8 bytes is below TMA's 16-byte minimum) travel as one 8-byte element each in a
+    // 3-D box whose x origin is rounded down by one record (16-byte aligned) and whose width
+    // TX + 2 keeps the row a multiple of 16 bytes
+    static constexpr bool CPACK = sizeof(C) == 2;
+    static constexpr int CBX = CPACK ? TX + 2 : TX + 1;    // records per landed row
+    static constexpr int CSHIFT = CPACK ? 1 : 0;           // landed position of corner ci is ci + CSHIFT
+    static constexpr int C_BYTES = (TY + 1) * CBX * 4 * (int)sizeof(C);
     static constexpr int E_BYTES = TY * TX * (int)sizeof(S);
     static constexpr int U_OFF = 0;
     static constexpr int C_OFF = NF * U_PITCH;
@@ -156,7 +163,8 @@ tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* 
         mbar_expect_tx(bar, L::TX_BYTES);
 #pragma unroll
         for (int f = 0; f < Field::NF; ++f) tma_load_3d(s + L::U_OFF + f * L::U_PITCH, &maps.halo[f], t.i0 - L::HX, t.j0 - 1, z, bar);
-        tma_load_4d(s + L::C_OFF, &maps.coef, 0, t.i0 - 1, t.j0 - 1, z, bar);
+        if constexpr (L::CPACK) tma_load_3d(s + L::C_OFF, &maps.coef, t.i0 - 2, t.j0 - 1, z, bar);
+        else tma_load_4d(s + L::C_OFF, &maps.coef, 0, t.i0 - 1, t.j0 - 1, z, bar);
 #pragma unroll
         for (int a = 0; a < Epi::NC; ++a) tma_load_3d(s + L::E_OFF + a * align128(L::E_BYTES), &maps.cen[a], t.i0, t.j0, z, bar);
     };
@@ -184,8 +192,8 @@ tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* 
     };
     // corner (ci, cj) of plane z = k0-1+q from field slots q (plane z) and q+1 (plane z+1)
     auto corner = [&](int cbuf, int q, int ci, int cj) -> A {
-        const C* cr = reinterpret_cast<const C*>(slot(q) + L::C_OFF) + 4 * (cj * (TX + 1) + ci);
-        const A ca = (A)cr[0], cb = (A)cr[1], cc = (A)cr[2], cw = (A)cr[3];
+        const C* cr = reinterpret_cast<const C*>(slot(q) + L::C_OFF) + 4 * (cj * L::CBX + ci + L::CSHIFT);
+        const A ca = cvt<A>(cr[0]), cb = cvt<A>(cr[1]), cc = cvt<A>(cr[2]), cw = cvt<A>(cr[3]);
         const int x0 = ci - 1 + L::HX;
         const A u000 = U(q, cj, x0), u100 = U(q, cj, x0 + 1);
         const A u010 = U(q, cj + 1, x0), u110 = U(q, cj + 1, x0 + 1);

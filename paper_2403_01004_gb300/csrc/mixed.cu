@@ -9,57 +9,18 @@
 #include <cmath>
 #include <cstring>
 
+#include "dfloat.cuh"
 #include "epilogues.cuh"
 #include "launch.h"
 #include "march.cuh"
 
 namespace pb {
 
-// ---- double-float arithmetic -------------------------------------------------------------------
-// A value held as the unevaluated sum hi + lo of two floats (|lo| <= ulp(hi) / 2), about 48
-// significant bits, computed on the float32 pipes (GB300 issues float64 at a small fraction of
-// the float32 rate).  Sums follow Knuth's two-sum and Dekker's fast two-sum (the accurate
-// double-float addition); products take the exact rounding error of hi * hi from a fused
-// multiply-add.  Every operation is an explicit round-to-nearest intrinsic, so the compiler
-// neither contracts nor reorders the error terms.
-struct dfloat {
-    float hi, lo;
-    dfloat() = default;
-    __device__ constexpr dfloat(float h) : hi(h), lo(0.f) {}
-    __device__ constexpr dfloat(float h, float l) : hi(h), lo(l) {}
-};
-
-__device__ __forceinline__ dfloat two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return dfloat(s, e);
-}
-__device__ __forceinline__ dfloat fast_two_sum(float a, float b) {   // |a| >= |b|
-    const float s = __fadd_rn(a, b);
-    return dfloat(s, __fsub_rn(b, __fsub_rn(s, a)));
-}
-__device__ __forceinline__ dfloat operator+(dfloat x, dfloat y) {
-    dfloat s = two_sum(x.hi, y.hi);
-    const dfloat t = two_sum(x.lo, y.lo);
-    s = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
-    return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
-}
-__device__ __forceinline__ dfloat operator-(dfloat x) { return dfloat(-x.hi, -x.lo); }
-__device__ __forceinline__ dfloat operator-(dfloat x, dfloat y) { return x + (-y); }
-__device__ __forceinline__ dfloat operator*(dfloat x, dfloat y) {
-    const float p = __fmul_rn(x.hi, y.hi);
-    float e = __fmaf_rn(x.hi, y.hi, -p);
-    e = __fmaf_rn(x.hi, y.lo, e);
-    e = __fmaf_rn(x.lo, y.hi, e);
-    return fast_two_sum(p, e);
-}
-__device__ __forceinline__ double to_double(dfloat x) { return (double)x.hi + (double)x.lo; }
 
 // float64 storage, double-float records and stencil arithmetic: the conduction residual of
 // mixed-precision Backward Euler (the kernel templates of the march take it as a policy)
-struct PolDF { using S = double; using C = dfloat; using A = dfloat; using E = double;
-               static constexpr int id = PB_FP64; static constexpr bool CG = false; };
+struct PolDF { using S = double; using C = dfloat; using A = dfloat; using E = double; using U = double;
+               static constexpr int id = PB_FP64; static constexpr bool CG = false; static constexpr bool DF = false; };
 
 template <> __device__ __forceinline__ dfloat cvt<dfloat, double>(double v) {
     const float h = __double2float_rn(v);
@@ -227,6 +188,7 @@ Ctx& mixed_shadow(Ctx& c) {
         s->kind = c.kind;
         s->prec = PB_FP32;
         s->elem = 4;
+        s->welem = 4;
         s->stream = c.stream;
         s->nr = c.nr; s->nt = c.nt; s->np = c.np;
         s->grid = c.grid;

@@ -3,6 +3,8 @@
 // coefficient records, the state and the output array for F.  The only scratch -- the per-block
 // arg-max partials, the non-finite flag and the result record -- lives in one file-scope device
 // array of fixed size, shared by every call on a device.
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <mutex>
 
@@ -24,23 +26,54 @@ static __device__ __align__(256) unsigned char g_ptl_scratch[kScratchBytes];
 
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};   // id of the context the address belongs to
 
-// Device address of the scratch array on the current device, looked up once per device (the
-// symbol's host-side name is only a stand-in and must never be handed to a kernel).
+PFN_cuCtxGetCurrent_v4000 g_ctx_current = nullptr;
+PFN_cuCtxGetId_v12000 g_ctx_id = nullptr;
+std::once_flag g_once;
+
+void resolve_driver() {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuCtxGetCurrent", &fn, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        g_ctx_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(fn);
+    fn = nullptr;
+    if (cudaGetDriverEntryPoint("cuCtxGetId", &fn, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        g_ctx_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(fn);
+    cudaGetLastError();
+}
+
+// Unique id of the current context (0 if unknown): a device reset tears the primary context
+// down, the library's module is loaded again in the new one and the array may move.
+unsigned long long current_ctx_id() {
+    std::call_once(g_once, resolve_driver);
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!g_ctx_current || !g_ctx_id || g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx || g_ctx_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of the scratch array on the current device, looked up on the first call in a
+// context (the symbol's host-side name is only a stand-in and must never be handed to a kernel).
 int scratch_address(void** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
         return PB_ECUDA;
     }
+    const unsigned long long ctx = current_ctx_id();
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    if (!g_scratch_addr[dev] || ctx == 0 || g_scratch_ctx[dev] != ctx) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_ptl_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
             return PB_ECUDA;
         }
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = current_ctx_id();   // the lookup made the device's context current
     }
     *out = g_scratch_addr[dev];
     return PB_OK;
@@ -87,11 +120,14 @@ bool make_grid(int kind, int nr, int nt, int np, int sm_count, MarchGrid& g, lon
     return blocks <= kMaxBlocks;
 }
 
+// P: the policy (records P::C, F written as P::S); the state is read as the caller's type P::U
 template <class P>
 int run(const MarchGrid& g, int kind, const void* rec, const void* u, void* F, unsigned char* scratch,
         cudaStream_t s) {
     using S = typename P::S;
     using C = typename P::C;
+    using U = typename P::U;
+    using Ld = LoadStateT<P, U>;
     ArgMax* part = reinterpret_cast<ArgMax*>(scratch + kPartOff);
     int* flag = reinterpret_cast<int*>(scratch + kFlagOff);
     PtlResult* res = reinterpret_cast<PtlResult*>(scratch + kResultOff);
@@ -99,14 +135,14 @@ int run(const MarchGrid& g, int kind, const void* rec, const void* u, void* F, u
     // are written in full by every call
     if (cudaMemsetAsync(flag, 0, sizeof(int), s) != cudaSuccess) return PB_ECUDA;
     EpiF<P, true, false> ep{static_cast<S*>(F), nullptr, typename P::A(0), part, flag};
-    const LoadState<P> ld{static_cast<const S*>(u)};
+    const Ld ld{static_cast<const U*>(u)};
     const Coef4<C>* cf = static_cast<const Coef4<C>*>(rec);
     if (kind == PB_TC_ANISO)
-        tc_march<P, LoadState<P>, EpiF<P, true, false>><<<g.nblocks, dim3(TX, TY), 0, s>>>(g, cf, ld, ep);
+        tc_march<P, Ld, EpiF<P, true, false>><<<g.nblocks, dim3(TX, TY), 0, s>>>(g, cf, ld, ep);
     else
-        visc_march<P, LoadState<P>, EpiF<P, true, false>><<<g.nblocks, dim3(TX, TY), 0, s>>>(g, cf, ld, ep);
-    ptl_finalize_kernel<P><<<1, kFinalizeThreads, 0, s>>>(g, static_cast<const S*>(u), static_cast<const S*>(F), part,
-                                            g.nblocks, res, flag);
+        visc_march<P, Ld, EpiF<P, true, false>><<<g.nblocks, dim3(TX, TY), 0, s>>>(g, cf, ld, ep);
+    ptl_finalize_kernel<P, U><<<1, kFinalizeThreads, 0, s>>>(g, static_cast<const U*>(u), static_cast<const S*>(F), part,
+                                               g.nblocks, res, flag);
     return cudaGetLastError() == cudaSuccess ? PB_OK : PB_ECUDA;
 }
 

@@ -16,12 +16,20 @@ namespace pb {
 template <class Epi> struct ViscCapped { static constexpr bool value = false; };
 template <bool U1> struct ViscCapped<EpiF<PolF32, true, U1>> { static constexpr bool value = true; };
 
+// Element-wise conversion between the caller's state type and the working precision.
+template <typename From, typename To>
+__global__ void convert_kernel(long long n, const From* in, To* out) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        out[t] = cvt<To>(ldg(in + t));
+}
+
 template <class P>
 class OpsImpl : public Ops {
     using S = typename P::S;
     using C = typename P::C;
     using A = typename P::A;
     using E = typename P::E;
+    using U = typename P::U;
 
     template <class Load, class Epi>
     static void march(Ctx& c, const void* coef, const Load& ld, const Epi& ep) {
@@ -53,7 +61,7 @@ class OpsImpl : public Ops {
             const CompGrid& g = c.grid.c[0];
             TmaMaps maps;
             bool ok = tma_state_map(&maps.halo[0], field, sizeof(S), g.nr, g.nt, g.np, L::BXW, TY + 2) &&
-                      tma_coef_map(&maps.coef, c.coef, sizeof(C), g.nr, g.nt, g.np, TX + 1, TY + 1);
+                      tma_coef_map(&maps.coef, c.coef, sizeof(C), g.nr, g.nt, g.np, L::CBX, TY + 1);
             for (int a = 0; ok && a < Epi::NC; ++a)
                 ok = tma_state_map(&maps.cen[a], cen[a], sizeof(S), g.nr, g.nt, g.np, TX, TY);
             if (ok) {
@@ -79,7 +87,7 @@ class OpsImpl : public Ops {
         const CompGrid& g = c.grid.c[0];
         TmaMaps maps;
         const void* f[3] = {c.r, c.dinv, pold};
-        bool ok = tma_coef_map(&maps.coef, c.coef_be, sizeof(C), g.nr, g.nt, g.np, TX + 1, TY + 1);
+        bool ok = tma_coef_map(&maps.coef, c.coef_be, sizeof(C), g.nr, g.nt, g.np, L::CBX, TY + 1);
         for (int a = 0; ok && a < 3; ++a) ok = tma_state_map(&maps.halo[a], f[a], sizeof(S), g.nr, g.nt, g.np, L::BXW, TY + 2);
         if (!ok) return false;
         const int smem = L::TOTAL + 128;
@@ -91,6 +99,9 @@ class OpsImpl : public Ops {
         PB_CUDA_TRY(cudaGetLastError());
         return true;
     }
+
+    // low part of a float64 coefficient under a double-float policy (x = (float)x + lo), else 0
+    static float lo_part(double x) { return P::DF ? (float)(x - (double)(float)x) : 0.f; }
 
 public:
     bool supports_pcg() const override { return P::id == PB_FP64 || P::id == PB_FP32; }
@@ -112,6 +123,7 @@ public:
             KScope ks(c.prof, c.stream, K_PTL_PASS, nb(c, u1 ? 3 : 2, 4));
             if (u1) {
                 EpiF<P, true, true> ep{static_cast<S*>(y0), static_cast<S*>(u1), (A)a, part, c.d_flag};
+                ep.al = lo_part(a);
                 march_state(c, u, nullptr, ep);
             } else {
                 EpiF<P, true, false> ep{static_cast<S*>(y0), nullptr, A(0), part, c.d_flag};
@@ -120,6 +132,7 @@ public:
         } else if (u1) {
             KScope ks(c.prof, c.stream, K_Y0_D1, nb(c, 3, 4));
             EpiF<P, false, true> ep{static_cast<S*>(y0), static_cast<S*>(u1), (A)a, nullptr, nullptr};
+            ep.al = lo_part(a);
             march_state(c, u, nullptr, ep);
         } else {
             apply(c, u, y0);
@@ -156,8 +169,12 @@ public:
     template <bool LAST>
     void stage2_t(Ctx& c, const void* y0, void* d1, const void* u0, void* out, double a1, const StageCoef& k) {
         KScope ks(c.prof, c.stream, K_STAGE, nb(c, 3, 4));
+        const double cy = k.mu * a1 + k.ydt, cf = k.mdt * a1;
         EpiStage2<P, LAST> ep{static_cast<const S*>(u0), static_cast<S*>(d1), static_cast<S*>(out), (E)a1,
-                              (E)(k.mu * a1 + k.ydt), (E)(k.mdt * a1), static_cast<const S*>(y0)};
+                              (E)cy, (E)cf, static_cast<const S*>(y0)};
+        ep.al = lo_part(a1);
+        ep.cyl = lo_part(cy);
+        ep.cfl = lo_part(cf);
         const void* cen[1] = {u0};
         march_state(c, y0, cen, ep);
     }
@@ -173,6 +190,10 @@ public:
         EpiStage<P, KM2, LAST> ep{static_cast<const S*>(dkm2), static_cast<const S*>(y0), static_cast<const S*>(u0),
                                   static_cast<S*>(out), (E)k.mu, (E)k.nu, (E)k.mdt, (E)k.ydt,
                                   static_cast<const S*>(dkm1)};
+        ep.mul = lo_part(k.mu);
+        ep.nul = lo_part(k.nu);
+        ep.mdtl = lo_part(k.mdt);
+        ep.ydtl = lo_part(k.ydt);
         KScope ks(c.prof, c.stream, K_STAGE, nb(c, 3 + (KM2 ? 1 : 0) + (LAST ? 1 : 0), 4));
         const void* cen[3];
         int n = 0;
@@ -232,6 +253,25 @@ public:
         PB_CUDA_TRY(cudaGetLastError());
     }
 
+    void* enter(Ctx& c, const void* u) override {
+        if constexpr (std::is_same<U, S>::value) {
+            return const_cast<void*>(u);
+        } else {
+            convert_kernel<U, S><<<reduce_blocks(c), 256, 0, c.stream>>>(c.n, static_cast<const U*>(u), static_cast<S*>(c.work));
+            PB_CUDA_TRY(cudaGetLastError());
+            return c.work;
+        }
+    }
+
+    void leave(Ctx& c, const void* w, void* u) override {
+        if constexpr (std::is_same<U, S>::value) {
+            if (w != u) PB_CUDA_TRY(cudaMemcpyAsync(u, w, (size_t)c.n * sizeof(S), cudaMemcpyDeviceToDevice, c.stream));
+        } else {
+            convert_kernel<S, U><<<reduce_blocks(c), 256, 0, c.stream>>>(c.n, static_cast<const S*>(w), static_cast<U*>(u));
+            PB_CUDA_TRY(cudaGetLastError());
+        }
+    }
+
     void store_coefs(Ctx& c, const Coef4<double>* rec, const double* adiag) override;
 };
 
@@ -242,10 +282,10 @@ __global__ void store_coefs_kernel(long long n, const Coef4<double>* rec, const 
     using C = typename P::C;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         const Coef4<double> r = rec[t];
-        out[t] = Coef4<C>{(C)r.a, (C)r.b, (C)r.c, (C)r.w};
+        out[t] = Coef4<C>{to_rec<C>(r.a), to_rec<C>(r.b), to_rec<C>(r.c), to_rec<C>(r.w)};
         // the Backward Euler record carries the mass M = 1/w instead of w
-        out_be[t] = Coef4<C>{(C)r.a, (C)r.b, (C)r.c, (C)(1.0 / r.w)};
-        adiag_out[t] = (C)adiag[t];
+        out_be[t] = Coef4<C>{to_rec<C>(r.a), to_rec<C>(r.b), to_rec<C>(r.c), to_rec<C>(1.0 / r.w)};
+        adiag_out[t] = to_rec<C>(adiag[t]);
     }
 }
 

@@ -66,7 +66,7 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
 // Host: the tensor maps one TMA march launch needs (all for one scalar field grid).
 struct TmaMaps {
     CUtensorMap halo[3];   // arrays of the input field, box (TX + 2 HX) x (TY + 2) x 1
-    CUtensorMap coef;      // coefficient records, box 4 x (TX + 1) x (TY + 1) x 1
+    CUtensorMap coef;      // coefficient records, box 4 x (TX + 1) x (TY + 1) x 1 (bfloat16: (TX + 2) x (TY + 1) x 1 records)
     CUtensorMap cen[3];    // point operands of the epilogue, box TX x TY x 1
 };
 
@@ -74,6 +74,8 @@ struct TmaMaps {
 // (row stride not a multiple of 16 bytes, or an unaligned base address).
 bool tma_available();
 bool tma_state_map(CUtensorMap* m, const void* base, int elem_bytes, int nr, int nt, int np, int box_x, int box_y);
+// elem_bytes 2 (bfloat16 records): a 3-D map of 8-byte records, needing n_r even (row stride a
+// multiple of 16 bytes).
 bool tma_coef_map(CUtensorMap* m, const void* base, int elem_bytes, int nr, int nt, int np, int box_x, int box_y);
 
 }  // namespace pb

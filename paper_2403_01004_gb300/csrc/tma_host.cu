@@ -56,6 +56,17 @@ bool tma_coef_map(CUtensorMap* m, const void* base, int elem, int nr, int nt, in
     if (!tma_available()) return false;
     if ((reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
     if (box_x > 256 || box_y > 256) return false;
+    if (elem == 2) {
+        // one 8-byte element per 4-word bfloat16 record (a raw copy: the type only sets the size)
+        if (((long long)nr * 8) % 16 != 0 || (box_x * 8) % 16 != 0) return false;
+        cuuint64_t d3[3] = {(cuuint64_t)nr, (cuuint64_t)nt, (cuuint64_t)np};
+        cuuint64_t s3[2] = {(cuuint64_t)8 * nr, (cuuint64_t)8 * nr * nt};
+        cuuint32_t b3[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
+        cuuint32_t e3[3] = {1, 1, 1};
+        return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void*>(base), d3, s3, b3, e3,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
     cuuint64_t dims[4] = {4, (cuuint64_t)nr, (cuuint64_t)nt, (cuuint64_t)np};
     cuuint64_t strides[3] = {(cuuint64_t)4 * elem, (cuuint64_t)4 * elem * nr, (cuuint64_t)4 * elem * nr * nt};
     cuuint32_t box[4] = {4, (cuuint32_t)box_x, (cuuint32_t)box_y, 1};

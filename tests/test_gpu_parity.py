@@ -1,10 +1,11 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle on the same seeded inputs.
 
 Tolerances (relative L2 of the result against the oracle): FP64 1e-12, FP32 1e-5, BF16 storage
-1e-2.  Operator applications (F = L u) are compared in the max norm relative to max |F|, with
-tolerances derived from the storage rounding of u amplified by the cancellation in the
-differences of neighbouring values (about 100x for 1% noise): FP64 1e-12, FP32 1e-4,
-BF16 3e-1 (BF16 only resolves 0.4% of a value)."""
+1e-2.  Operator applications (F = L u, the oracle on the same rounded u) are compared in the max
+norm relative to max |F|: FP64 1e-12; FP32 1e-4 (float32 rounding of the records and of the
+arithmetic, amplified by the cancellation in the differences of neighbouring values); BF16
+storage 3e-2 (the records rounded to bfloat16, 2^-9 relative, a few per point, and F handed back
+in bfloat16)."""
 import math
 
 import numpy as np
@@ -17,7 +18,7 @@ from oracle.ptl import ptl, ptl_full
 
 pytestmark = pytest.mark.gpu
 
-APPLY_TOL = {"fp64": 1e-12, "fp32": 1e-4, "bf16": 3e-1}
+APPLY_TOL = {"fp64": 1e-12, "fp32": 1e-4, "bf16": 3e-2}
 # several tiles in r (32) and theta (8), ragged tails, phi chunking with wrap
 SHAPES = [(40, 21, 13), (32, 32, 64), (2, 2, 3), (67, 9, 5)]
 
@@ -45,7 +46,7 @@ def test_tc_apply(shape, prec):
 
 
 @pytest.mark.parametrize("shape", SHAPES)
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
 def test_visc_apply(shape, prec):
     import paper_2403_01004_gb300 as pb
     g, vi, op, v = visc_problem(*shape)
@@ -213,8 +214,6 @@ def test_sts_reduced_precision_forced_schedule(kind, prec):
     comparison isolates the arithmetic precision from the (discontinuous) cycle decisions.
     fp64s (float64 storage, float32 stencil) is held to the float32 tolerance: its stencil
     arithmetic is float32."""
-    if kind == "visc" and prec == "bf16":
-        pytest.skip("bf16 storage targets the conduction workload")
     shape = (32, 32, 64) if kind == "tc" else (24, 20, 16)
     g, inp, op, u = tc_problem(*shape) if kind == "tc" else visc_problem(*shape)
     _, log = sts_advance(op, u, 100.0 * op.dt_explicit(), "rkl2", use_ptl=True)
@@ -315,7 +314,9 @@ def test_tma_and_fallback_kernels_agree(prec, monkeypatch):
         ud = to_dev(u, ctx)
         pb.rkl2_advance(ctx, ud, dt, use_ptl=True)
         outs.append(to_host(ud))
-    assert rel_l2(outs[0], outs[1]) <= {"fp64": 1e-14, "fp32": 1e-6, "bf16": 1e-2, "fp64s": 1e-6}[prec]
+    # same arithmetic, compiled in two kernels (the compiler may contract the corner sums
+    # differently); bfloat16 storage rounds the two float32 results once at the end
+    assert rel_l2(outs[0], outs[1]) <= {"fp64": 1e-14, "fp32": 1e-6, "bf16": 1e-3, "fp64s": 1e-6}[prec]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
