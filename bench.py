@@ -293,6 +293,9 @@ def run_ours(args):
     pb.pb_profile_enable(ctx_v, False)
     step_stats = {k: dict(cycles=v_["cycles"], stages=v_["total_stages"]) for k, v_ in stats.items()}
     value = units / (ms / 1e3)
+    # the timed step's results and cycle schedules (every step starts from the same inputs)
+    result = {"tc": u.clone(), "visc": v.clone()}
+    schedule = {k: list(v_["dt_cycle"]) for k, v_ in stats.items()}
     launches = sum(p["launches"] for p in prof)
 
     e2e = None
@@ -327,6 +330,11 @@ def run_ours(args):
     kernels = kernel_table(prof)
 
     extra = {}
+    if not args.no_fp64 and args.precision != "fp64":
+        extra["fp64_plain"], extra["accuracy"] = fp64_probe(pb, torch, g, d_tc, d_vi, d_u0, d_v0, wl, args, value,
+                                                            result, schedule)
+        extra["accuracy"]["oracle_first_cycle"] = oracle_first_cycle_probe(pb, torch, g, tc, ctx_tc, d_u0,
+                                                                           schedule["tc"][0], args)
     if not args.no_rkg2 and args.scheme == "rkl2":
         # the paper's own scheme (Appendix A) on the same step: same kernels, its coefficients
         # and odd stage counts; its stronger high-mode damping changes the PTL schedule
@@ -337,6 +345,13 @@ def run_ours(args):
         args.scheme = prev
         extra["rkg2_step"] = {"value": units_g / (ms_g / 1e3), "unit": UNIT, "ms_per_step": ms_g,
                               "step": {k: dict(cycles=v_["cycles"], stages=v_["total_stages"]) for k, v_ in stats.items()}}
+    # time per step decides the comparison of the schemes (point-stage updates/s rewards a
+    # schedule of many short cycles); both schemes' steps, with each operator's cycles and stages
+    step_time = {args.scheme: {"ms": ms / args.steps, **step_stats}}
+    if "rkg2_step" in extra:
+        step_time["rkg2"] = {"ms": extra["rkg2_step"]["ms_per_step"], **extra["rkg2_step"]["step"]}
+    if "fp64_plain" in extra:
+        step_time[f"{args.scheme}_fp64_plain"] = {"ms": extra["fp64_plain"]["ms_per_step"], **extra["fp64_plain"]["step"]}
     if not args.no_ptl_study:
         extra["ptl_study"] = ptl_study_probe(pb, torch, ctx_tc, ctx_v, d_u0, d_v0, wl)
     if not args.no_stress:
@@ -349,8 +364,6 @@ def run_ours(args):
         extra["batched"] = batched_probe(pb, torch)
     if not args.no_learned:
         extra["learned_guess"] = learned_probe(pb, torch)
-    if not args.no_fp64 and args.precision != "fp64":
-        extra["fp64_plain"] = fp64_probe(pb, torch, g, d_tc, d_vi, d_u0, d_v0, wl, args, value)
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(g, tc, vi, wl, step_stats, n_tc, n_v)
@@ -359,7 +372,8 @@ def run_ours(args):
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "step_time": step_time,
+        "accuracy": extra.pop("accuracy", None), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16-storage/f32"}[args.precision],
         "data": "synthetic (seeded dipole shell; stand-in for the paper's MAS Test 2 state)",
@@ -384,7 +398,7 @@ def kernel_table(prof):
 
 
 KERNEL_SOURCES = ("common.cuh", "prof.h", "reduce.cuh", "march.cuh", "march_tma.cuh", "tma.cuh",
-                  "epilogues.cuh", "ops_impl.cuh")
+                  "epilogues.cuh", "ops_impl.cuh", "dfloat.cuh")
 
 
 def source_hash() -> str:
@@ -723,8 +737,11 @@ def precision_stress_probe(pb, torch, bf16_cap=5000):
     return out
 
 
-def fp64_probe(pb, torch, g, d_tc, d_vi, d_u0, d_v0, wl, args, value32):
-    """The same step with float64 storage and arithmetic (the plain FP64 GPU path), timed once."""
+def fp64_probe(pb, torch, g, d_tc, d_vi, d_u0, d_v0, wl, args, value32, result, schedule):
+    """The same step with float64 storage and arithmetic (the plain FP64 GPU path), timed once,
+    and the error of the timed step's results against it: relative L2 against the float64 run of
+    the timed step's own cycle schedule (the precision alone), and against the float64 step with
+    its own PTL decisions (precision and schedule together)."""
     c1 = pb.parabolic_setup(g.r_face, g.t_face, g.n_phi, "tc", d_tc, "fp64")
     c2 = pb.parabolic_setup(g.r_face, g.t_face, g.n_phi, "visc", d_vi, "fp64")
     u = d_u0.to(torch.float64)
@@ -739,11 +756,63 @@ def fp64_probe(pb, torch, g, d_tc, d_vi, d_u0, d_v0, wl, args, value32):
     ms = e0.elapsed_time(e1)
     units = c1.n * s1["total_stages"] + c2.n * s2["total_stages"]
     val = units / (ms / 1e3)
+
+    def rel(a, b):
+        a = a.to(torch.float64)
+        return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+    acc = {"what": f"relative L2 of the timed {args.precision} step's results against the float64 GPU path",
+           "tolerance": {"fp32": 1e-5, "bf16": 1e-2}.get(args.precision)}
+    own = {"tc": (s1, u), "visc": (s2, v)}
+    for name, ctx, x0 in (("tc", c1, d_u0), ("visc", c2, d_v0)):
+        st64, x64 = own[name]
+        same = list(st64["dt_cycle"]) == schedule[name] or (
+            len(st64["dt_cycle"]) == len(schedule[name]) and
+            all(abs(a - b) <= 1e-12 * abs(b) for a, b in zip(st64["dt_cycle"], schedule[name])))
+        xf = x0.to(torch.float64)
+        pb.rkl2_advance(ctx, xf, 0.0, scheme=args.scheme, forced=schedule[name])
+        acc[name] = {"same_schedule_rel_l2": rel(result[name], xf),
+                     "own_ptl_rel_l2": rel(result[name], x64),
+                     "schedules_equal": bool(same), "cycles": len(schedule[name]), "cycles_fp64": st64["cycles"]}
     c1.close()
     c2.close()
-    return {"value": val, "unit": UNIT, "ms_per_step": ms, "speedup_of_main": value32 / val,
-            "step": {"tc": dict(cycles=s1["cycles"], stages=s1["total_stages"]),
-                     "visc": dict(cycles=s2["cycles"], stages=s2["total_stages"])}}
+    return ({"value": val, "unit": UNIT, "ms_per_step": ms, "speedup_of_main": value32 / val,
+             "step": {"tc": dict(cycles=s1["cycles"], stages=s1["total_stages"]),
+                      "visc": dict(cycles=s2["cycles"], stages=s2["total_stages"])}}, acc)
+
+
+def oracle_first_cycle_probe(pb, torch, g, tc, ctx, d_u0, dt_c, args):
+    """The timed step's first conduction cycle (its own length and stage count) at sampled points
+    against the float64 oracle's stages on windows of the grid: after s stages a point depends
+    only on points within s cells, so a window of margin s + 1 reproduces the full-grid result
+    there (windows on the r boundaries, the poles and the phi wrap)."""
+    from oracle.geometry import Shell
+    from oracle.sts import rkl2_coefficients, rkg2_coefficients, sts_step
+    from oracle.tc import TCOperator
+    n_r, n_t, n_p = g.n_r, g.n_theta, g.n_phi
+    x = d_u0.clone()
+    st = pb.rkl2_advance(ctx, x, 0.0, scheme=args.scheme, forced=[dt_c])
+    s = st["work_cycle"][0]
+    co = (rkl2_coefficients if args.scheme == "rkl2" else rkg2_coefficients)(s)
+    xh = x.to(torch.float64).cpu().numpy().reshape(n_p, n_t, n_r)
+    uh = d_u0.to(torch.float64).cpu().numpy().reshape(n_p, n_t, n_r)
+    m = s + 1
+    got, ref = [], []
+    for (k, j, i) in [(0, 0, 0), (n_p - 1, n_t - 1, n_r - 1), (37, n_t // 2, 3), (n_p // 2, 1, n_r * 3 // 4)]:
+        i0, i1 = max(0, i - m), min(n_r, i + m + 1)
+        j0, j1 = max(0, j - m), min(n_t, j + m + 1)
+        ks = [(k + d) % n_p for d in range(-m, m + 1)]
+        sl = lambda a: a[ks][:, j0:j1, i0:i1]
+        sh = Shell(g.r_face[i0:i1 + 1], g.t_face[j0:j1 + 1], len(ks), dphi=2 * np.pi / n_p)
+        op = TCOperator.spherical(sh, sl(tc.T), sl(tc.n), [sl(b) for b in tc.B])
+        uw = sl(uh).reshape(-1)
+        xo = sts_step(op.apply, uw, op.apply(uw), dt_c, co).reshape(op.shape)
+        got.append(xh[k, j, i])
+        ref.append(xo[m, j - j0, i - i0])
+    got, ref = np.array(got), np.array(ref)
+    return {"what": "first conduction cycle of the step at 4 sampled points (boundaries, poles, wrap) "
+                    "against the float64 oracle on windows", "stages": s,
+            "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
 
 
 # ---- CPU oracle -------------------------------------------------------------------------------

@@ -68,7 +68,8 @@ extern "C" {
  * PB_BF16_STORE: bfloat16 storage with float32 accumulation -- the caller's state arrays and
  * the operator's coefficient records are bfloat16; within a call the state and the stage values
  * are float32 (a context-owned working copy), with the PB_FP32 stage recurrence; the state is
- * rounded to bfloat16 once, when the call hands it back (STS, apply and PTL only).
+ * rounded to bfloat16 once, when the call hands it back (STS, apply and PTL only).  dt_E of a
+ * PB_BF16_STORE context is the Gershgorin bound of the operator on its rounded records.
  * PB_FP64_STORE: float64 states and stage recurrence, float32 records and stencil arithmetic
  * (STS only; BE + PCG needs PB_FP64 or PB_FP32). */
 typedef enum { PB_FP64 = 0, PB_FP32 = 1, PB_BF16_STORE = 2, PB_FP64_STORE = 3 } pb_precision;

@@ -53,20 +53,18 @@ __device__ __forceinline__ double to_double(dfloat x) { return (double)x.hi + (d
 // recurrence loses nothing to its own arithmetic (or to the float rounding of its coefficients);
 // only the store of the result rounds.
 struct DfAcc {
-    float s = 0.f, e = 0.f;
+    float s, e;
+    // starts the sum with c v
+    __device__ __forceinline__ void set(float ch, float cl, float v) {
+        s = __fmul_rn(ch, v);
+        e = __fmaf_rn(cl, v, __fmaf_rn(ch, v, -s));
+    }
     __device__ __forceinline__ void add(float ch, float cl, float v) {
         const float p = __fmul_rn(ch, v);
-        float err = __fmaf_rn(ch, v, -p);
-        err = __fmaf_rn(cl, v, err);
+        const float err = __fmaf_rn(cl, v, __fmaf_rn(ch, v, -p));
         const dfloat t = two_sum(s, p);
         s = t.hi;
         e = __fadd_rn(e, __fadd_rn(t.lo, err));
-    }
-    // add a float value exactly (the state u_0 of the last stage)
-    __device__ __forceinline__ void add(float v) {
-        const dfloat t = two_sum(s, v);
-        s = t.hi;
-        e = __fadd_rn(e, t.lo);
     }
     __device__ __forceinline__ float value() const { return __fadd_rn(s, e); }
 };

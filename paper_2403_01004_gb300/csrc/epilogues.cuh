@@ -122,10 +122,11 @@ struct EpiF {
 // + mut dt F(u_{k-1}) + gt dt y_0; it drops the u_0 read from every stage but the last and
 // keeps stored stage values small (the rounding of reduced-precision storage acts on d, not u).
 // The last stage writes u_s = u_0 + d_s over u_0 in place (each point is read before it is
-// written, by the same thread).  Under a double-float policy (P::DF) the right-hand side, u_0
-// included, is summed in double-float with the float64 coefficients split into float pairs, so
-// the stage adds one rounding, the store's (float32 arithmetic would add several, at the
-// magnitude of the largest term: in the stiff modes mdt F and ydt y_0 nearly cancel).
+// written, by the same thread).  Under a double-float policy (P::DF) the increment's right-hand
+// side is summed in double-float with the float64 coefficients split into float pairs, so the
+// stage adds one rounding, the store's (float32 arithmetic would add several, at the magnitude
+// of the largest term: in the stiff modes mdt F and ydt y_0 nearly cancel); the last stage then
+// adds the increment to u_0 in float, one more rounding per cycle.
 template <class P, bool KM2, bool LAST>
 struct EpiStage {
     using A = typename P::A;
@@ -159,12 +160,12 @@ struct EpiStage {
     __device__ void update(long long idx, A Au, A w, E d1, E d2, E y, E u) {
         if constexpr (P::DF) {
             DfAcc acc;
-            acc.add(mu, mul, d1);
+            acc.set(mu, mul, d1);
             if (KM2) acc.add(nu, nul, d2);
             acc.add(mdt, mdtl, __fmul_rn(w, Au));
             acc.add(ydt, ydtl, y);
-            if (LAST) acc.add(u);
-            out[idx] = cvt<S>(acc.value());
+            // the last stage adds the increment to u_0 once: one more rounding per cycle, not per stage
+            out[idx] = cvt<S>(LAST ? __fadd_rn(u, acc.value()) : acc.value());
         } else {
             const E d = mu * d1 + nu * d2 + mdt * (E)(w * Au) + ydt * y;
             out[idx] = cvt<S>(LAST ? u + d : d);
@@ -201,15 +202,20 @@ struct EpiStage2 {
     __device__ void apply(long long idx, A Au, A w, A y, const Pre& p) { update(idx, Au, w, kExact ? p.y : (E)y, p.u0); }
     __device__ void update(long long idx, A Au, A w, E y, E u) {
         if constexpr (P::DF) {
-            DfAcc acc;
-            acc.add(cy, cyl, y);
-            acc.add(cf, cfl, __fmul_rn(w, Au));
+            // two terms: the product cy y split exactly (FMA error term), cf F added to it by one
+            // fused multiply-add, so the two nearly cancelling terms of the stiff modes are summed
+            // exactly and d2 is rounded at its own magnitude (the error terms, coefficients' low
+            // parts included, added after)
+            const float F = __fmul_rn(w, Au);
+            const float p = __fmul_rn(cy, y);
+            const float err = __fmaf_rn(cfl, F, __fmaf_rn(cyl, y, __fmaf_rn(cy, y, -p)));
+            const float d2 = __fadd_rn(__fmaf_rn(cf, F, p), err);
             if (LAST) {
-                acc.add(u);
+                out[idx] = cvt<S>(__fadd_rn(u, d2));
             } else {
                 d1[idx] = cvt<S>(df_scale(a, al, y));
+                out[idx] = cvt<S>(d2);
             }
-            out[idx] = cvt<S>(acc.value());
         } else {
             const E d2 = cy * y + cf * (E)(w * Au);
             if (LAST) {

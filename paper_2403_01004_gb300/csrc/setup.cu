@@ -327,6 +327,27 @@ void setup_geometry(Ctx& c, const pb_grid& g) {
     }
 }
 
+// bfloat16-storage contexts: the float64 records rounded to the values the kernels will read, so
+// that dt_E (the Gershgorin bound) and diag(A) belong to the operator actually applied.  A
+// bfloat16 record may lie 2^-9 above its float64 value, and at the PTL floor a cycle runs at
+// exactly the forward-Euler limit (RKL2 s = 2 has |R| = 1 there): a bound taken from the unrounded
+// operator lets the highest modes grow by about 2^-8 per cycle.
+__global__ void round_records_bf16_kernel(long long n, Coef4<double>* rec) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        Coef4<double> r = rec[t];
+        r.a = (double)__bfloat162float(__double2bfloat16(r.a));
+        r.b = (double)__bfloat162float(__double2bfloat16(r.b));
+        r.c = (double)__bfloat162float(__double2bfloat16(r.c));
+        r.w = (double)__bfloat162float(__double2bfloat16(r.w));
+        rec[t] = r;
+    }
+}
+
+static void round_records(Ctx& c, Coef4<double>* rec, long long n) {
+    if (c.prec != PB_BF16_STORE) return;
+    round_records_bf16_kernel<<<setup_blocks(c, n), 256, 0, c.stream>>>(n, rec);
+}
+
 void setup_tc(Ctx& c, const pb_operator& op, Coef4<double>* rec, double* dt_e) {
     const long long n = c.n;
     double* kap = c.s64;
@@ -336,6 +357,7 @@ void setup_tc(Ctx& c, const pb_operator& op, Coef4<double>* rec, double* dt_e) {
     const bool box = c.geometry == PB_CARTESIAN_PERIODIC;
     if (box) tc_coef_box_kernel<<<blocks, 256, 0, c.stream>>>(a);
     else tc_coef_kernel<<<blocks, 256, 0, c.stream>>>(a);
+    round_records(c, rec, n);
     double* part = static_cast<double*>(c.partials);
     double* adiag = c.s64;   // kappa is no longer needed
     tc_rows_kernel<<<blocks, 256, 0, c.stream>>>(c.nr, c.nt, c.np, box ? 1 : 0, rec, adiag, part);
@@ -358,6 +380,12 @@ void setup_visc(Ctx& c, const pb_operator& op, Coef4<double>* rec, double* dt_e)
         const int blocks = setup_blocks(c, n);
         if (cg.periodic) visc_coef_box_kernel<<<blocks, 256, 0, c.stream>>>(a);
         else visc_coef_kernel<<<blocks, 256, 0, c.stream>>>(a);
+    }
+    round_records(c, rec, c.n);
+    for (int comp = 0; comp < 3; ++comp) {
+        const CompGrid& cg = c.grid.c[comp];
+        const long long n = (long long)cg.nr * cg.nt * cg.np;
+        const int blocks = setup_blocks(c, n);
         visc_rows_kernel<<<blocks, 256, 0, c.stream>>>(cg.nr, cg.nt, cg.np, cg.periodic, rec + cg.offset,
                                                        adiag + cg.offset, part + total_blocks);
         total_blocks += blocks;

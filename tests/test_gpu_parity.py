@@ -19,6 +19,9 @@ from oracle.ptl import ptl, ptl_full
 pytestmark = pytest.mark.gpu
 
 APPLY_TOL = {"fp64": 1e-12, "fp32": 1e-4, "bf16": 3e-2}
+# dt_E is the Gershgorin bound of the operator the context applies: bfloat16 storage bounds the
+# operator on its rounded records (each 2^-9 relative at most from the float64 one)
+DTE_TOL = {"fp64": 1e-13, "fp32": 1e-13, "bf16": 8e-3}
 # several tiles in r (32) and theta (8), ragged tails, phi chunking with wrap
 SHAPES = [(40, 21, 13), (32, 32, 64), (2, 2, 3), (67, 9, 5)]
 
@@ -42,7 +45,7 @@ def test_tc_apply(shape, prec):
     F = to_host(pb.parabolic_apply(ctx, ud))
     Fo = op.apply(to_host(ud))      # oracle on the same (rounded) input
     assert rel_max(F, Fo) <= APPLY_TOL[prec], rel_max(F, Fo)
-    assert pb.parabolic_dt_explicit(ctx) == pytest.approx(op.dt_explicit(), rel=1e-13 if prec == "fp64" else 1e-13)
+    assert pb.parabolic_dt_explicit(ctx) == pytest.approx(op.dt_explicit(), rel=DTE_TOL[prec])
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -55,7 +58,7 @@ def test_visc_apply(shape, prec):
     F = to_host(pb.parabolic_apply(ctx, vd))
     Fo = op.apply(to_host(vd))
     assert rel_max(F, Fo) <= APPLY_TOL[prec], rel_max(F, Fo)
-    assert pb.parabolic_dt_explicit(ctx) == pytest.approx(op.dt_explicit(), rel=1e-13)
+    assert pb.parabolic_dt_explicit(ctx) == pytest.approx(op.dt_explicit(), rel=DTE_TOL[prec])
 
 
 @pytest.mark.parametrize("kind", ["tc", "visc"])
@@ -218,7 +221,8 @@ def test_sts_reduced_precision_forced_schedule(kind, prec):
     g, inp, op, u = tc_problem(*shape) if kind == "tc" else visc_problem(*shape)
     _, log = sts_advance(op, u, 100.0 * op.dt_explicit(), "rkl2", use_ptl=True)
     st, log2, ug, uo, _, _ = _sts_compare(kind, shape, "rkl2", prec, forced=log.dt_c)
-    assert st["work_cycle"] == log2.s
+    if prec != "bf16":      # bfloat16 storage: stage counts from its own dt_E (rounded records)
+        assert st["work_cycle"] == log2.s
     tol = TOL["fp32" if prec == "fp64s" else prec]
     assert rel_l2(ug, uo) <= tol, rel_l2(ug, uo)
 
