@@ -226,6 +226,17 @@ PB_API int rkl2_advance(pb_ctx* ctx, void* u_dev, double dt, const pb_advance_op
  * next synchronous call. */
 PB_API int rkl2_advance_async(pb_ctx* ctx, void* u_dev, double dt, const pb_advance_opts* opts);
 
+/* Non-linear conduction under RKL2 / RKG2 (Sec. 3.1: super time stepping handles a non-linear
+ * operator; Sec. 2: the diffusivity is lagged): before every cycle the coefficients are
+ * recomputed with kappa = max(T, 0)^{5/2} from the current state T, with dt_E, and the cycle --
+ * its PTL decision and its stages -- runs with that operator frozen.  The cycle rule, options and
+ * statistics are those of rkl2_advance (no floor-cycle speculation; ptl_mode PB_PTL_FMAX only;
+ * stats->dt_explicit is the last cycle's).  op: the conduction operator's n, B and C (device
+ * float64, read every cycle; op->T0 is not read).  On return the context holds the coefficients
+ * of the last cycle's operator.  Conduction contexts only (PB_EINVAL otherwise). */
+PB_API int rkl2_advance_relag(pb_ctx* ctx, void* u_dev, double dt, const pb_advance_opts* opts,
+                              const pb_operator* op, pb_stats* stats);
+
 /* Advances u (device, in place) over dt with Backward Euler, each cycle solving
  * (M - dt_c A) x = M u (M = diag(1/w), F = w A u) by point-Jacobi PCG from x0 = u, or from
  * x0_dev (device, ctx precision) on the first cycle when it is not NULL.  Supported for

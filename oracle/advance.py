@@ -105,6 +105,52 @@ def sts_advance(op, u, dt: float, scheme: str = "rkl2", use_ptl: bool = True, fo
     return u, log
 
 
+def sts_advance_relag(build, u, dt: float, scheme: str = "rkl2", use_ptl: bool = True, forced=None,
+                      max_cycles: int = 100000, floor: float = 1.0):
+    """Non-linear conduction with the diffusivity re-lagged every cycle.  Sec. 3.1 notes that super
+    time stepping can handle a non-linear operator, and Sec. 2 freezes kappa at a lagged
+    temperature; reading fixed by the project: before every cycle the operator is rebuilt from
+    the current state, build(T0) with T0 = max(u, 0) (kappa = T0^{5/2}; a state that undershoots
+    zero gets no negative diffusivity), dt_E is re-evaluated from it, and the cycle -- its PTL
+    decision and its s stages -- runs with that operator frozen.  The cycle rule is that of
+    sts_advance.  Returns (u_new, CycleLog, dt_E of the last cycle's operator)."""
+    stages, coeffs = SCHEMES[scheme]
+    u = np.array(u, dtype=np.float64, copy=True)
+    log = CycleLog()
+    t_rem, c, dtE = dt, 0, math.nan
+    while True:
+        if forced is not None:
+            if c >= len(forced):
+                break
+        elif not t_rem > 1e-12 * dt:
+            break
+        elif c >= max_cycles:
+            raise MaxCyclesError(f"more than {max_cycles} cycles")
+        op = build(np.maximum(u, 0.0))
+        dtE = op.dt_explicit()
+        F = op.apply(u)
+        dtp, k = math.nan, -1
+        if forced is not None:
+            dt_c = float(forced[c])
+        elif use_ptl:
+            dtp, k, _ = ptl(op, u, F)
+            dtl = max(dtp, floor * dtE)
+            q = t_rem / dtl * TIE
+            n = 1.0 if q <= 1.0 else math.ceil(q)
+            dt_c = t_rem / n
+        else:
+            dt_c = t_rem
+        s = stages(dt_c / dtE)
+        u = sts_step(op.apply, u, F, dt_c, coeffs(s))
+        log.dt_c.append(dt_c)
+        log.s.append(s)
+        log.dt_ptl.append(dtp)
+        log.k.append(k)
+        t_rem -= dt_c
+        c += 1
+    return u, log, dtE
+
+
 def be_advance(op, u, dt: float, use_ptl: bool = True, rtol: float = 1e-10, max_iter: int = 100000,
                forced=None, max_cycles: int = 100000, fixed_iters: int = 0, floor: float = 1.0,
                ptl_mode: str = "fmax"):

@@ -32,7 +32,8 @@ C_TC = (5.0 / 3.0 - 1.0) / 2.0
 # C function names exported by the library (kept in step with include/parabolic.h)
 EXPORTS = ("pb_advance_opts_init", "pb_status_string", "pb_last_error", "parabolic_setup",
            "parabolic_update", "parabolic_destroy", "parabolic_state_size", "parabolic_dt_explicit", "parabolic_apply",
-           "ptl_compute", "ptl_full_compute", "rkl2_advance", "rkl2_advance_async", "be_pcg_advance", "pb_profile_enable", "pb_profile_read",
+           "ptl_compute", "ptl_full_compute", "rkl2_advance", "rkl2_advance_async", "rkl2_advance_relag",
+           "be_pcg_advance", "pb_profile_enable", "pb_profile_read",
            "pb_ptl_noalloc", "pb_tune_init", "pb_batch_create", "pb_batch_destroy", "pb_batch_last_error",
            "pb_batch_rkl2_advance", "pb_autotune", "pb_model_create", "pb_model_destroy", "pb_model_last_error",
            "pb_model_num_params", "pb_model_get_params", "pb_model_set_params", "pb_model_save", "pb_model_load",
@@ -113,6 +114,9 @@ def load_library(path: str = LIB_PATH):
     lib.ptl_compute.argtypes = [c_void_p, c_void_p, POINTER(c_double), POINTER(c_int64), POINTER(c_double)]
     lib.rkl2_advance.argtypes = [c_void_p, c_void_p, c_double, POINTER(PbAdvanceOpts), POINTER(PbStats)]
     lib.rkl2_advance_async.argtypes = [c_void_p, c_void_p, c_double, POINTER(PbAdvanceOpts)]
+    lib.rkl2_advance_relag.argtypes = [c_void_p, c_void_p, c_double, POINTER(PbAdvanceOpts), POINTER(PbOperator),
+                                       POINTER(PbStats)]
+    lib.rkl2_advance_relag.restype = c_int32
     lib.ptl_full_compute.argtypes = [c_void_p, c_void_p, POINTER(c_double), POINTER(c_int64), POINTER(c_int32)]
     lib.be_pcg_advance.argtypes = [c_void_p, c_void_p, c_double, POINTER(PbAdvanceOpts), c_void_p, POINTER(PbStats)]
     lib.pb_ptl_noalloc.argtypes = [c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
@@ -393,6 +397,28 @@ def rkl2_advance(ctx: Context, u, dt: float, scheme: str = "rkl2", use_ptl: bool
     o, keep = _opts(scheme, use_ptl, max_cycles, ptl_floor, forced, ptl_mode=ptl_mode)
     sb = _StatsBuf(stats_capacity, record_full)
     rc = load_library().rkl2_advance(ctx.handle, c_void_p(_ptr(u)), float(dt), byref(o), byref(sb.st))
+    d = sb.as_dict()
+    d["status"] = rc
+    if raise_on_error:
+        _check(rc, ctx.handle)
+    return d
+
+
+def rkl2_advance_relag(ctx: Context, u, dt: float, fields: dict, scheme: str = "rkl2", use_ptl: bool = True,
+                       forced=None, max_cycles: int = 0, ptl_floor: float = 1.0, stats_capacity: int = 4096,
+                       raise_on_error: bool = True) -> dict:
+    """Non-linear conduction: like rkl2_advance, with the coefficients recomputed before every
+    cycle from kappa = max(T, 0)^{5/2} of the current state; fields gives n and B (float64 CUDA
+    tensors; T0 is not read)."""
+    _check_state(ctx, u)
+    if ctx.kind != "tc":
+        raise ValueError("the re-lag is for conduction contexts")
+    f = dict(fields)
+    f.setdefault("T0", f["n"])
+    op, keep_op = _operator("tc", f, getattr(ctx, "C", C_TC))
+    o, keep = _opts(scheme, use_ptl, max_cycles, ptl_floor, forced)
+    sb = _StatsBuf(stats_capacity)
+    rc = load_library().rkl2_advance_relag(ctx.handle, c_void_p(_ptr(u)), float(dt), byref(o), byref(op), byref(sb.st))
     d = sb.as_dict()
     d["status"] = rc
     if raise_on_error:

@@ -632,6 +632,81 @@ int rkl2_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, pb_
     return rc;
 }
 
+int rkl2_advance_relag(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, const pb_operator* op,
+                       pb_stats* st) {
+    if (!h) return PB_EINVAL;
+    Ctx& c = h->c;
+    stats_begin(st, c);
+    int cycle = 0;
+    void* wu = nullptr;
+    const int rc = guarded(&c, [&] {
+        const pb_advance_opts o = resolve(opts);
+        if (!u) throw Error{PB_EINVAL, "null state pointer"};
+        if (!(dt >= 0.0) || std::isinf(dt)) throw Error{PB_EINVAL, "dt must be finite and >= 0"};
+        if (c.kind != PB_TC_ANISO) throw Error{PB_EINVAL, "the per-cycle re-lag is for conduction contexts"};
+        if (!op || op->kind != PB_TC_ANISO || !op->n || !op->B[0] || !op->B[1] || !op->B[2] || !(op->C > 0.0))
+            throw Error{PB_EINVAL, "the re-lag needs the operator's n, B and C"};
+        if (o.ptl_mode != PB_PTL_FMAX) throw Error{PB_EINVAL, "the re-lag cycles under Eq. 5"};
+        Ops* ops = ops_of(c);
+        wu = ops->enter(c, u);
+        const bool forced = o.n_forced > 0;
+        double t_rem = dt;
+        Sts co;
+        for (cycle = 0;; ++cycle) {
+            if (forced) {
+                if (cycle >= o.n_forced) break;
+            } else {
+                if (!(t_rem > 1e-12 * dt)) break;
+                if (cycle >= o.max_cycles) throw Error{PB_EMAXCYCLES, "PTL cycle count above max_cycles"};
+            }
+            // the operator of this cycle: kappa = max(T, 0)^{5/2} from the current state, the
+            // records and dt_E from it, frozen for the cycle
+            ops->to_f64(c, wu, c.s64);
+            pb_operator lag = *op;
+            lag.T0 = c.s64;
+            setup_tc(c, lag, c.coef64, &c.dt_e, true);
+            ops->store_coefs(c, c.coef64, c.s64);
+            mixed_refresh(c);
+            sync(c);
+            if (!(c.dt_e > 0.0) || std::isinf(c.dt_e)) throw Error{PB_ENONFINITE, "dt_E is not a positive finite number"};
+            if (st) st->dt_explicit = c.dt_e;
+            double dt_c, dtp = std::numeric_limits<double>::quiet_NaN();
+            long long kk = -1;
+            if (forced) {
+                dt_c = o.dt_cycles[cycle];
+                if (!(dt_c >= 0.0) || std::isinf(dt_c)) throw Error{PB_EINVAL, "forced cycle length must be finite and >= 0"};
+                ops->apply(c, wu, c.y0);
+            } else if (o.use_ptl) {
+                const PtlResult r = run_ptl(c, ops, wu);
+                if (r.nonfinite) throw Error{PB_ENONFINITE, "non-finite F in the PTL pass"};
+                dtp = r.dt_ptl;
+                kk = r.k;
+                if (st) { st->last_dt_ptl = dtp; st->fmax = r.fmax; st->k_index = r.k; }
+                dt_c = cycle_length(t_rem, dtp, o.ptl_floor * c.dt_e);
+            } else {
+                dt_c = t_rem;
+                ops->apply(c, wu, c.y0);
+            }
+            make_sts(o.scheme, dt_c / c.dt_e, co);
+            enqueue_stages(c, ops, co, dt_c, wu, wu);
+            if (st) st->total_stages += co.s;
+            stats_cycle(st, dt_c, co.s, dtp, kk, std::numeric_limits<double>::quiet_NaN());
+            t_rem -= dt_c;
+        }
+        if (wu != u) ops->leave(c, wu, u);
+        sync(c);
+    });
+    if (rc != PB_OK && wu && wu != u) {
+        try {
+            ops_of(c)->leave(c, wu, u);
+        } catch (const Error&) {
+        }
+        cudaStreamSynchronize(c.stream);
+    }
+    if (rc != PB_OK && st) st->status_cycle = cycle;
+    return rc;
+}
+
 int be_pcg_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, const void* x0, pb_stats* st) {
     if (!h) return PB_EINVAL;
     Ctx& c = h->c;

@@ -41,6 +41,8 @@ public:
     virtual void leave(Ctx& c, const void* work, void* u) = 0;
     // converts the float64 coefficient records into the context's storage precision
     virtual void store_coefs(Ctx& c, const Coef4<double>* rec, const double* adiag) = 0;
+    // a working state widened to float64 (the lagged temperature of a per-cycle coefficient update)
+    virtual void to_f64(Ctx& c, const void* work, double* out) = 0;
     virtual bool supports_pcg() const = 0;
 };
 
@@ -51,7 +53,8 @@ Ops* ops_f64s();   // PolF64S: float64 storage and recurrence, float32 stencil
 
 // set-up kernels (float64), see setup.cu.  setup_tc / setup_visc leave diag(A) in c.s64.
 void setup_geometry(Ctx& c, const pb_grid& g);
-void setup_tc(Ctx& c, const pb_operator& op, Coef4<double>* rec, double* dt_e);
+// clamp: kappa = max(T0, 0)^{5/2} (T0 may be c.s64 itself)
+void setup_tc(Ctx& c, const pb_operator& op, Coef4<double>* rec, double* dt_e, bool clamp = false);
 void setup_visc(Ctx& c, const pb_operator& op, Coef4<double>* rec, double* dt_e);
 
 int reduce_blocks(const Ctx& c);   // grid size of the element-wise reduction kernels

@@ -272,6 +272,11 @@ public:
         }
     }
 
+    void to_f64(Ctx& c, const void* w, double* out) override {
+        convert_kernel<S, double><<<reduce_blocks(c), 256, 0, c.stream>>>(c.n, static_cast<const S*>(w), out);
+        PB_CUDA_TRY(cudaGetLastError());
+    }
+
     void store_coefs(Ctx& c, const Coef4<double>* rec, const double* adiag) override;
 };
 

@@ -10,9 +10,11 @@ namespace pb {
 
 namespace {
 
-__global__ void kappa_kernel(long long n, const double* T0, double* kap) {
+// kappa = T0^{5/2}; with clamp, max(T0, 0)^{5/2} (the lagged diffusivity of a state that may
+// undershoot zero; kap may alias T0)
+__global__ void kappa_kernel(long long n, const double* T0, double* kap, bool clamp) {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-        const double T = T0[t];
+        const double T = clamp ? fmax(T0[t], 0.0) : T0[t];
         kap[t] = T * T * sqrt(T);          // T0^{5/2}
     }
 }
@@ -348,11 +350,11 @@ static void round_records(Ctx& c, Coef4<double>* rec, long long n) {
     round_records_bf16_kernel<<<setup_blocks(c, n), 256, 0, c.stream>>>(n, rec);
 }
 
-void setup_tc(Ctx& c, const pb_operator& op, Coef4<double>* rec, double* dt_e) {
+void setup_tc(Ctx& c, const pb_operator& op, Coef4<double>* rec, double* dt_e, bool clamp) {
     const long long n = c.n;
     double* kap = c.s64;
     const int blocks = setup_blocks(c, n);
-    kappa_kernel<<<blocks, 256, 0, c.stream>>>(n, op.T0, kap);
+    kappa_kernel<<<blocks, 256, 0, c.stream>>>(n, op.T0, kap, clamp);
     TCArgs a{c.nr, c.nt, c.np, 2.0 * M_PI / c.np, op.C, c.geo[0], c.geo[1], kap, op.n, op.B[0], op.B[1], op.B[2], rec};
     const bool box = c.geometry == PB_CARTESIAN_PERIODIC;
     if (box) tc_coef_box_kernel<<<blocks, 256, 0, c.stream>>>(a);
