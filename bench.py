@@ -428,15 +428,23 @@ def traffic_for(kernel: str, args):
 
 
 def pcg_probe(pb, torch, g, d_tc, d_u0, wl):
-    """Backward Euler + point-Jacobi PCG on the same conduction problem, float64 state, to
-    rtol 1e-10: one cycle of dt = 1e3 dt_E with plain float64 PCG and with mixed precision
-    (float64 residuals, float32 corrections), and the whole step under PTL cycling (mixed)."""
+    """Backward Euler + PCG on the same conduction problem, float64 state, to rtol 1e-10: one
+    cycle of dt = 1e3 dt_E with plain float64 PCG and with mixed precision (float64 residuals,
+    float32 corrections), and the whole step under PTL cycling (mixed); each with point-Jacobi
+    (PC1) and with the Chebyshev polynomial preconditioner of degree m (m - 1 extra stencil
+    passes per iteration)."""
     ctx = pb.parabolic_setup(g.r_face, g.t_face, g.n_phi, "tc", d_tc, "fp64")
     u0 = d_u0.to(torch.float64)
     dt = wl["ratio"] * pb.parabolic_dt_explicit(ctx)
     out = {"what": "BE + PC1 PCG, shell256 conduction, float64 state, rtol 1e-10"}
+    cheb = lambda m: dict(precond="chebyshev", pc_degree=m)
     for name, kw in (("one_cycle_fp64", dict(use_ptl=False)), ("one_cycle_mixed", dict(use_ptl=False, mixed=True)),
-                     ("ptl_step_mixed", dict(use_ptl=True, mixed=True))):
+                     ("ptl_step_mixed", dict(use_ptl=True, mixed=True)),
+                     ("one_cycle_fp64_cheb3", dict(use_ptl=False, **cheb(3))),
+                     ("one_cycle_mixed_cheb2", dict(use_ptl=False, mixed=True, **cheb(2))),
+                     ("one_cycle_mixed_cheb3", dict(use_ptl=False, mixed=True, **cheb(3))),
+                     ("one_cycle_mixed_cheb4", dict(use_ptl=False, mixed=True, **cheb(4))),
+                     ("ptl_step_mixed_cheb3", dict(use_ptl=True, mixed=True, **cheb(3)))):
         u = u0.clone()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

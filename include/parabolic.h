@@ -78,6 +78,12 @@ typedef enum { PB_RKL2 = 0, PB_RKG2 = 1 } pb_scheme;
 /* Where the PTL condition is evaluated: at argmax |F| only (Eq. 5) or over every pair of face
  * neighbours (Eq. 4 without the F_max localisation; Sec. 2, the text after Eq. 4). */
 typedef enum { PB_PTL_FMAX = 0, PB_PTL_FULL = 1 } pb_ptl_mode;
+/* Preconditioner of the Backward Euler PCG (Sec. 3.1 names point-Jacobi PC1 and the stronger,
+ * incomplete-factorisation PC2).  PB_PC_CHEBYSHEV is this library's GPU form of a stronger
+ * preconditioner: z = p(D^-1 S) D^-1 r with p the degree-m Chebyshev acceleration of point-Jacobi
+ * on [b/30, b], b = 1.05 x the Gershgorin bound of D^-1 S for the cycle; fewer iterations (and
+ * global dot products) for m - 1 extra stencil passes per iteration. */
+typedef enum { PB_PC_JACOBI = 0, PB_PC_CHEBYSHEV = 1 } pb_precond;
 
 typedef struct pb_ctx pb_ctx;
 
@@ -135,6 +141,9 @@ typedef struct {
                                  the last correction stops once the outer test is met)      */
     int32_t ptl_mode;         /* PB_PTL_FMAX (default) or PB_PTL_FULL: the PTL value that
                                  sets each cycle                                            */
+    int32_t precond;          /* BE: PB_PC_JACOBI (default, PC1) or PB_PC_CHEBYSHEV          */
+    int32_t pc_degree;        /* BE with PB_PC_CHEBYSHEV: polynomial degree m, 2..32 (default 3):
+                                 m - 1 stencil passes per application                        */
 } pb_advance_opts;
 
 /* Statistics of an advance call (host struct).  The per-cycle arrays are optional caller-owned
@@ -244,7 +253,10 @@ PB_API int rkl2_advance_relag(pb_ctx* ctx, void* u_dev, double dt, const pb_adva
  * With opts->mixed_precision on a PB_FP64 conduction context the outer residuals that drive
  * the refinements are computed in double-float arithmetic (about 48 bits, on the float32
  * pipes), and a cycle stops only when the float64 residual meets rtol; environment
- * PB_MIXED_FP64_RESIDUAL=1 (read at each call) uses float64 residuals throughout. */
+ * PB_MIXED_FP64_RESIDUAL=1 (read at each call) uses float64 residuals throughout.
+ * opts->precond = PB_PC_CHEBYSHEV preconditions the PCG polynomially (with mixed_precision, the
+ * float32 inner solves); stats count its PCG iterations, each of which runs pc_degree - 1 extra
+ * stencil passes. */
 PB_API int be_pcg_advance(pb_ctx* ctx, void* u_dev, double dt, const pb_advance_opts* opts,
                    const void* x0_dev, pb_stats* stats);
 

@@ -153,15 +153,16 @@ def sts_advance_relag(build, u, dt: float, scheme: str = "rkl2", use_ptl: bool =
 
 def be_advance(op, u, dt: float, use_ptl: bool = True, rtol: float = 1e-10, max_iter: int = 100000,
                forced=None, max_cycles: int = 100000, fixed_iters: int = 0, floor: float = 1.0,
-               ptl_mode: str = "fmax"):
-    """Advance u over dt with Backward Euler + PCG and PTL cycling."""
+               ptl_mode: str = "fmax", precond: str = "jacobi", degree: int = 3):
+    """Advance u over dt with Backward Euler + PCG (point-Jacobi, or the Chebyshev polynomial
+    preconditioner of oracle.pcg) and PTL cycling."""
     u = np.array(u, dtype=np.float64, copy=True)
     log = CycleLog()
     gen = _cycles(op, u, dt, use_ptl, forced, max_cycles, log, False, floor, ptl_mode)
     try:
         dt_c, _ = next(gen)
         while True:
-            res = be_solve(op, u, dt_c, rtol, max_iter, fixed_iters=fixed_iters)
+            res = be_solve(op, u, dt_c, rtol, max_iter, fixed_iters=fixed_iters, precond=precond, degree=degree)
             u = res.x
             log.iters.append(res.iters)
             log.true_res.append(res.true_rel_residual)

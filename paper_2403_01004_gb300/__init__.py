@@ -55,7 +55,7 @@ class PbAdvanceOpts(ctypes.Structure):
                 ("ptl_floor", c_double), ("dt_cycles", POINTER(c_double)), ("n_forced", c_int32),
                 ("rtol", c_double), ("max_iter", c_int32), ("fixed_iters", c_int32),
                 ("check_every", c_int32), ("judge_guess", c_int32), ("mixed_precision", c_int32),
-                ("inner_rtol", c_double), ("ptl_mode", c_int32)]
+                ("inner_rtol", c_double), ("ptl_mode", c_int32), ("precond", c_int32), ("pc_degree", c_int32)]
 
 
 class PbStats(ctypes.Structure):
@@ -333,9 +333,12 @@ def ptl_full_compute(ctx: Context, u):
     return dt.value, cell.value, d.value
 
 
+PRECONDS = {"jacobi": 0, "chebyshev": 1}
+
+
 def _opts(scheme="rkl2", use_ptl=True, max_cycles=0, ptl_floor=1.0, forced=None, rtol=1e-10,
           max_iter=100000, fixed_iters=0, check_every=8, judge_guess=True, mixed=False, inner_rtol=1e-3,
-          ptl_mode="fmax"):
+          ptl_mode="fmax", precond="jacobi", pc_degree=3):
     lib = load_library()
     o = PbAdvanceOpts()
     lib.pb_advance_opts_init(byref(o))
@@ -356,6 +359,8 @@ def _opts(scheme="rkl2", use_ptl=True, max_cycles=0, ptl_floor=1.0, forced=None,
     o.mixed_precision = 1 if mixed else 0
     o.inner_rtol = float(inner_rtol)
     o.ptl_mode = PTL_MODES[ptl_mode]
+    o.precond = PRECONDS[precond]
+    o.pc_degree = int(pc_degree)
     return o, keep
 
 
@@ -439,13 +444,15 @@ def be_pcg_advance(ctx: Context, u, dt: float, use_ptl: bool = True, forced=None
                    max_iter: int = 100000, fixed_iters: int = 0, x0=None, max_cycles: int = 0,
                    ptl_floor: float = 1.0, check_every: int = 8, stats_capacity: int = 4096,
                    raise_on_error: bool = True, judge_guess: bool = True, mixed: bool = False,
-                   inner_rtol: float = 1e-3, ptl_mode: str = "fmax", record_full: bool = False) -> dict:
-    """Advances u in place over dt with Backward Euler + point-Jacobi PCG under PTL cycling.
-    With x0 (first cycle's initial guess) and judge_guess, the solve starts from whichever of
-    x0 and u has the smaller initial residual."""
+                   inner_rtol: float = 1e-3, ptl_mode: str = "fmax", record_full: bool = False,
+                   precond: str = "jacobi", pc_degree: int = 3) -> dict:
+    """Advances u in place over dt with Backward Euler + PCG under PTL cycling, preconditioned by
+    point-Jacobi (precond "jacobi", PC1) or by the degree-pc_degree Chebyshev polynomial in
+    D^-1 S ("chebyshev").  With x0 (first cycle's initial guess) and judge_guess, the solve
+    starts from whichever of x0 and u has the smaller initial residual."""
     _check_state(ctx, u)
     o, keep = _opts("rkl2", use_ptl, max_cycles, ptl_floor, forced, rtol, max_iter, fixed_iters, check_every,
-                    judge_guess, mixed, inner_rtol, ptl_mode)
+                    judge_guess, mixed, inner_rtol, ptl_mode, precond, pc_degree)
     sb = _StatsBuf(stats_capacity, record_full)
     x0p = c_void_p(_ptr(x0)) if x0 is not None else c_void_p(0)
     rc = load_library().be_pcg_advance(ctx.handle, c_void_p(_ptr(u)), float(dt), byref(o), x0p, byref(sb.st))

@@ -92,6 +92,9 @@ void free_ctx(Ctx& c) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c.s64) cudaFree(c.s64);
+    if (c.arow) cudaFree(c.arow);
+    for (void* p : c.cheb)
+        if (p) cudaFree(p);
     for (double* p : c.geo)
         if (p) cudaFree(p);
     if (c.h_ptl) cudaFreeHost(c.h_ptl);
@@ -157,6 +160,9 @@ pb_advance_opts resolve(const pb_advance_opts* o) {
     if (!(r.inner_rtol > 0.0) || !(r.inner_rtol < 1.0)) r.inner_rtol = 1e-3;
     if (r.scheme != PB_RKL2 && r.scheme != PB_RKG2) throw Error{PB_EINVAL, "unknown scheme"};
     if (r.ptl_mode != PB_PTL_FMAX && r.ptl_mode != PB_PTL_FULL) throw Error{PB_EINVAL, "unknown ptl_mode"};
+    if (r.precond != PB_PC_JACOBI && r.precond != PB_PC_CHEBYSHEV) throw Error{PB_EINVAL, "unknown precond"};
+    if (r.precond == PB_PC_CHEBYSHEV && r.pc_degree <= 1) r.pc_degree = 3;
+    if (r.pc_degree > 32) throw Error{PB_EINVAL, "pc_degree above 32"};
     if (r.dt_cycles == nullptr) r.n_forced = 0;
     if (r.n_forced < 0) throw Error{PB_EINVAL, "n_forced < 0"};
     return r;
@@ -258,6 +264,24 @@ void enqueue_stages(Ctx& c, Ops* ops, const Sts& co, double dt_c, const void* in
     }
 }
 
+// The Chebyshev preconditioner of a cycle: interval [b/30, b] with b = 1.05 x the Gershgorin
+// bound of D^-1 S, and the coefficients of the three-term recurrence (cheb.cuh).
+ChebPlan cheb_plan(double bound, int m) {
+    ChebPlan pl;
+    pl.m = m;
+    const double b = 1.05 * bound, a = b / 30.0;
+    const double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
+    pl.inv_theta = 1.0 / theta;
+    double rho_prev = 1.0 / sigma;
+    for (int j = 1; j < m; ++j) {
+        const double rho = 1.0 / (2.0 * sigma - rho_prev);
+        pl.c1[j] = rho * rho_prev;
+        pl.c2[j] = 2.0 * rho / delta;
+        rho_prev = rho;
+    }
+    return pl;
+}
+
 // Decides the next cycle length (Sec. 2): returns false when the step is complete.
 struct CycleState {
     double dt, t_rem;
@@ -288,6 +312,8 @@ void pb_advance_opts_init(pb_advance_opts* o) {
     o->mixed_precision = 0;
     o->inner_rtol = 1e-3;
     o->ptl_mode = PB_PTL_FMAX;
+    o->precond = PB_PC_JACOBI;
+    o->pc_degree = 3;
 }
 
 const char* pb_status_string(int s) {
@@ -378,6 +404,7 @@ int parabolic_setup(const pb_grid* g, const pb_operator* op, int32_t precision, 
             PB_CUDA_TRY(cudaMemsetAsync(c.counter, 0, sizeof(unsigned int), c.stream));
             PB_CUDA_TRY(cudaMemsetAsync(c.d_flag, 0, sizeof(int), c.stream));
             c.s64 = static_cast<double*>(dmalloc((size_t)c.n * sizeof(double)));
+            c.arow = static_cast<double*>(dmalloc((size_t)c.n * sizeof(double)));
             setup_geometry(c, *g);
             update_coefficients(c, *op);
         } catch (...) {
@@ -718,6 +745,7 @@ int be_pcg_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, c
         if (!(dt >= 0.0) || std::isinf(dt)) throw Error{PB_EINVAL, "dt must be finite and >= 0"};
         Ops* ops = ops_of(c);
         if (!ops->supports_pcg()) throw Error{PB_ENOTSUP, "BE + PCG needs PB_FP64 or PB_FP32 contexts"};
+        const bool cheb = o.precond == PB_PC_CHEBYSHEV;
         ensure_pcg_buffers(c);
         const bool forced = o.n_forced > 0;
         const bool want_full = o.ptl_mode == PB_PTL_FULL || (st && st->dt_full_cycle);
@@ -785,7 +813,13 @@ int be_pcg_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, c
             } else {
                 init();
             }
-            if (o.mixed_precision && c.prec == PB_FP64 && o.fixed_iters <= 0) {
+            ChebPlan plan;
+            const bool refine = o.mixed_precision && c.prec == PB_FP64 && o.fixed_iters <= 0;
+            if (cheb) {
+                plan = cheb_plan(ops->cheb_bound(c, dt_c), o.pc_degree);
+                if (!refine) ops->pcg_precond(c, plan, dt_c);      // z_0 = P r_0 and <r_0, z_0>
+            }
+            if (refine) {
                 // iterative refinement: float64 residual (the set-up pass above) and float32
                 // corrections until r.r <= rtol^2 b.b
                 long long inner = 0;
@@ -811,7 +845,8 @@ int be_pcg_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, c
                     const double need = 0.25 * std::sqrt(now.tol2 * now.bb / now.rr);
                     if (need > tau) tau = std::min(need, 0.5);
                     int status = 0;
-                    inner += mixed_inner(c, u, dt_c, tau, o.max_iter - inner, o.check_every, &status);
+                    inner += mixed_inner(c, u, dt_c, tau, o.max_iter - inner, o.check_every, &status,
+                                         cheb ? &plan : nullptr);
                     ++refine;
                     if (status == 2) {
                         c.h_pcg->done = 2;
@@ -827,7 +862,8 @@ int be_pcg_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, c
                     sync(c);
                     if (c.h_pcg->done) break;
                     for (int m = 0; m < o.check_every; ++m) {
-                        ops->pcg_iter(c, u, parity, dt_c);
+                        if (cheb) ops->pcg_iter_poly(c, u, parity, dt_c, plan);
+                        else ops->pcg_iter(c, u, parity, dt_c);
                         parity ^= 1;
                     }
                 }

@@ -168,6 +168,8 @@ struct Ctx {
     double* h_scalar = nullptr;
     // persistent set-up workspace (coefficient updates allocate nothing)
     double* s64 = nullptr;         // float64 scratch [n]: kappa, then diag(A)
+    double* arow = nullptr;        // sum_j |A_ij| per row (float64) [n]: the Chebyshev bound
+    void* cheb[3] = {nullptr, nullptr, nullptr};   // Chebyshev preconditioner: z and the y ring
     double* geo[16] = {};          // device copies of the face / point coordinate arrays
     Prof prof;
     struct Ctx* shadow = nullptr;  // float32 shadow for mixed-precision BE (float64 contexts)

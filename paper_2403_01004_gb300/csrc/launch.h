@@ -8,6 +8,14 @@ namespace pb {
 // d_k = mu d_{k-1} + nu d_{k-2} + mdt F(d_{k-1}) + ydt y0   (increment form, see EpiStage)
 struct StageCoef { double mu, nu, mdt, ydt; };
 
+// The Chebyshev preconditioner of one Backward Euler cycle (see cheb.cuh): degree m, 1/theta, and
+// the coefficients c1[j] = rho_j rho_{j-1}, c2[j] = 2 rho_j / delta of passes j = 1 .. m-1.
+struct ChebPlan {
+    int m = 0;
+    double inv_theta = 0.0;
+    double c1[32] = {}, c2[32] = {};
+};
+
 class Ops {
 public:
     virtual ~Ops() {}
@@ -33,6 +41,11 @@ public:
     // PCG: set-up from x (in place) and u^n; one SpMV + update iteration
     virtual void pcg_init(Ctx& c, const void* x, const void* un, double dt) = 0;
     virtual void pcg_iter(Ctx& c, void* x, int parity, double dt) = 0;
+    // Chebyshev-preconditioned PCG: the bound b of the spectrum of D^-1 S for step dt (host
+    // value); z = P r with <r, z> and beta; one iteration (product, update, preconditioner)
+    virtual double cheb_bound(Ctx& c, double dt) = 0;
+    virtual void pcg_precond(Ctx& c, const ChebPlan& pl, double dt) = 0;
+    virtual void pcg_iter_poly(Ctx& c, void* x, int parity, double dt, const ChebPlan& pl) = 0;
     // The state the kernels work on: the caller's array itself, or, under bfloat16 storage, the
     // context's float32 working copy (c.work) filled from it
     virtual void* enter(Ctx& c, const void* u) = 0;
@@ -64,6 +77,8 @@ Ctx& mixed_shadow(Ctx& c);
 void mixed_refresh(Ctx& c);            // the shadow's records from the current float64 ones
 void mixed_residual(Ctx& c, const void* x, const void* un, double dt);   // conduction, double-float
 void free_shadow(Ctx* s);
-long long mixed_inner(Ctx& c, void* x, double dt, double inner_rtol, long long max_iter, int check_every, int* status);
+// plan: Chebyshev-preconditioned inner solves (nullptr: point-Jacobi)
+long long mixed_inner(Ctx& c, void* x, double dt, double inner_rtol, long long max_iter, int check_every, int* status,
+                      const ChebPlan* plan = nullptr);
 
 }  // namespace pb

@@ -252,7 +252,7 @@ void mixed_residual(Ctx& c, const void* x, const void* un, double dt) {
 void free_shadow(Ctx* s) {
     if (!s) return;
     void* p[] = {s->coef, s->coef_be, s->adiag, s->r, s->p[0], s->p[1], s->q, s->dinv, s->y0, s->partials,
-                 s->counter, s->d_pcg, s->coef64};
+                 s->counter, s->d_pcg, s->coef64, s->cheb[0], s->cheb[1], s->cheb[2]};
     for (void* q : p)
         if (q) cudaFree(q);
     if (s->h_pcg) cudaFreeHost(s->h_pcg);
@@ -263,7 +263,8 @@ void free_shadow(Ctx* s) {
 // One refinement's inner solve: S d = r (c.r, float64) to relative residual inner_rtol with at
 // most max_iter float32 PCG iterations, then x += d.  Returns the inner iterations; sets
 // *status to 0 (ok), 2 (non-finite) or 3 (cap reached, which the outer loop tolerates).
-long long mixed_inner(Ctx& c, void* x, double dt, double inner_rtol, long long max_iter, int check_every, int* status) {
+long long mixed_inner(Ctx& c, void* x, double dt, double inner_rtol, long long max_iter, int check_every, int* status,
+                      const ChebPlan* plan) {
     Ctx& s = mixed_shadow(c);
     PcgScalars& h = *s.h_pcg;
     std::memset(&h, 0, sizeof(h));
@@ -285,12 +286,14 @@ long long mixed_inner(Ctx& c, void* x, double dt, double inner_rtol, long long m
     }
     int parity = 0;
     Ops* ops = ops_f32();
+    if (plan) ops->pcg_precond(s, *plan, dt);      // z_0 = P r_0 (Chebyshev inner solves)
     for (;;) {
         PB_CUDA_TRY(cudaMemcpyAsync(s.h_pcg, s.d_pcg, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s.stream));
         PB_CUDA_TRY(cudaStreamSynchronize(s.stream));
         if (s.h_pcg->done) break;
         for (int m = 0; m < check_every; ++m) {
-            ops->pcg_iter(s, s.y0, parity, dt);
+            if (plan) ops->pcg_iter_poly(s, s.y0, parity, dt, *plan);
+            else ops->pcg_iter(s, s.y0, parity, dt);
             parity ^= 1;
         }
     }
@@ -307,6 +310,7 @@ long long mixed_inner(Ctx& c, void* x, double dt, double inner_rtol, long long m
     c.prof.absorb(s.prof, K_PCG_SPMV, K_PCG32_SPMV);
     c.prof.absorb(s.prof, K_PCG_UPDATE, K_PCG32_UPDATE);
     c.prof.absorb(s.prof, K_PCG32_REFINE, K_PCG32_REFINE);
+    c.prof.absorb(s.prof, K_PCG_CHEB, K_PCG_CHEB);
     return r.iter;
 }
 

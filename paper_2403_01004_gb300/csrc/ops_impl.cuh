@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "cheb.cuh"
 #include "epilogues.cuh"
 #include "launch.h"
 #include "march.cuh"
@@ -103,7 +104,122 @@ class OpsImpl : public Ops {
     // low part of a float64 coefficient under a double-float policy (x = (float)x + lo), else 0
     static float lo_part(double x) { return P::DF ? (float)(x - (double)(float)x) : 0.f; }
 
+    // A conduction march through the TMA kernel on field Fld (its NF arrays) with the epilogue's
+    // point operands; false when an array cannot be described by a tensor map.
+    template <class Epi, class Fld>
+    static bool tma_march(Ctx& c, const void* coef, const void* const* fields, const void* const* cen, const Epi& ep,
+                          const Fld& fld) {
+        if (c.kind != PB_TC_ANISO || !c.use_tma) return false;
+        using L = TmaLayout<P, Epi::NC, Fld>;
+        const CompGrid& g = c.grid.c[0];
+        TmaMaps maps;
+        bool ok = tma_coef_map(&maps.coef, coef, sizeof(C), g.nr, g.nt, g.np, L::CBX, TY + 1);
+        for (int a = 0; ok && a < Fld::NF; ++a) ok = tma_state_map(&maps.halo[a], fields[a], sizeof(S), g.nr, g.nt, g.np, L::BXW, TY + 2);
+        for (int a = 0; ok && a < Epi::NC; ++a) ok = tma_state_map(&maps.cen[a], cen[a], sizeof(S), g.nr, g.nt, g.np, TX, TY);
+        if (!ok) return false;
+        const int smem = L::TOTAL + 128;
+        static const cudaError_t attr = cudaFuncSetAttribute(tc_march_tma<P, Epi, Fld>,
+                                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        PB_CUDA_TRY(attr);
+        tc_march_tma<P, Epi, Fld><<<c.grid.nblocks, dim3(TX, TY), smem, c.stream>>>(c.grid, maps, ep, c.d_err, fld);
+        PB_CUDA_TRY(cudaGetLastError());
+        return true;
+    }
+
+    static void* ensure_cheb(Ctx& c, int i) {
+        if (!c.cheb[i]) {
+            void* p = nullptr;
+            if (cudaMalloc(&p, (size_t)c.n * sizeof(S)) != cudaSuccess) {
+                cudaGetLastError();
+                throw Error{PB_ENOMEM, "cudaMalloc of a Chebyshev vector failed"};
+            }
+            c.cheb[i] = p;
+        }
+        return c.cheb[i];
+    }
+
+    // Chebyshev pass j (1 .. m-1) of the preconditioner
+    template <int KIND, bool LAST>
+    static void cheb_pass(Ctx& c, const ChebPlan& pl, int j, double dt) {
+        S* r = static_cast<S*>(c.r);
+        S* dinv = static_cast<S*>(c.dinv);
+        S* out = static_cast<S*>(LAST ? c.cheb[0] : c.cheb[1 + (j + 1) % 2]);
+        const S* y = static_cast<const S*>(c.cheb[1 + j % 2]);          // y_j (j >= 2)
+        const S* yprev = static_cast<const S*>(c.cheb[1 + (j - 1) % 2]);   // y_{j-1} (j >= 3)
+        EpiCheb<P, KIND, LAST> ep{r, dinv, KIND == 3 ? yprev : nullptr, out, (A)dt, (A)pl.c1[j], (A)pl.c2[j],
+                                  (A)pl.inv_theta, c.d_pcg, static_cast<double*>(c.partials), c.counter,
+                                  c.grid.nblocks, 0, {0.0}};
+        const void* cen[3] = {r, dinv, yprev};
+        KScope ks(c.prof, c.stream, K_PCG_CHEB, nb(c, KIND == 1 ? 3 : (KIND == 2 ? 4 : 5), 4));
+        if constexpr (KIND == 1) {
+            const void* f[2] = {r, dinv};
+            if (!tma_march(c, c.coef_be, f, cen, ep, ChebY1Field<P>{(A)pl.inv_theta}))
+                march(c, c.coef_be, LoadChebY1<P>{r, dinv, (A)pl.inv_theta}, ep);
+        } else {
+            const void* f[1] = {y};
+            if (!tma_march(c, c.coef_be, f, cen, ep, PlainField<P>{}))
+                march(c, c.coef_be, LoadState<P>{y}, ep);
+        }
+    }
+
 public:
+    double cheb_bound(Ctx& c, double dt) override {
+        const int blocks = reduce_blocks(c);
+        cheb_bound_kernel<P><<<blocks, 256, 0, c.stream>>>(c.n, c.coef64, static_cast<const C*>(c.adiag), c.arow, dt,
+                                                           static_cast<double*>(c.partials));
+        max_partials_kernel<<<1, 256, 0, c.stream>>>(static_cast<const double*>(c.partials), blocks, c.d_scalar);
+        PB_CUDA_TRY(cudaGetLastError());
+        PB_CUDA_TRY(cudaMemcpyAsync(c.h_scalar, c.d_scalar, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        PB_CUDA_TRY(cudaStreamSynchronize(c.stream));
+        return *c.h_scalar;
+    }
+
+    void pcg_precond(Ctx& c, const ChebPlan& pl, double dt) override {
+        for (int i = 0; i < 3; ++i) ensure_cheb(c, i);
+        const int m = pl.m;
+        for (int j = 1; j < m; ++j) {
+            const bool last = j == m - 1;
+            if (j == 1) last ? cheb_pass<1, true>(c, pl, j, dt) : cheb_pass<1, false>(c, pl, j, dt);
+            else if (j == 2) last ? cheb_pass<2, true>(c, pl, j, dt) : cheb_pass<2, false>(c, pl, j, dt);
+            else last ? cheb_pass<3, true>(c, pl, j, dt) : cheb_pass<3, false>(c, pl, j, dt);
+        }
+    }
+
+    void pcg_iter_poly(Ctx& c, void* x, int parity, double dt, const ChebPlan& pl) override {
+        S* pold = static_cast<S*>(c.p[parity]);
+        S* pnew = static_cast<S*>(c.p[parity ^ 1]);
+        const S* z = static_cast<const S*>(c.cheb[0]);
+        EpiPcgSpmv<P> ep{pnew, static_cast<S*>(c.q), c.d_pcg, static_cast<double*>(c.partials), c.counter,
+                         c.grid.nblocks, (A)dt};
+        {
+            KScope ks(c.prof, c.stream, K_PCG_SPMV, nb(c, 4, 4));
+            const void* f[2] = {z, pold};
+            if (!tma_march(c, c.coef_be, f, nullptr, ep, PolyPField<P>{c.d_pcg, A(0), 0}))
+                march(c, c.coef_be, LoadPolyP<P>{z, pold, c.d_pcg, A(0), 0}, ep);
+        }
+        {
+            const int blocks = reduce_blocks(c);
+            KScope ks(c.prof, c.stream, K_PCG_UPDATE, nb(c, 6, 0));
+            bool vec = false;
+            if constexpr (std::is_same<S, float>::value && std::is_same<A, float>::value) {
+                const uintptr_t a = reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(c.r) |
+                                    reinterpret_cast<uintptr_t>(pnew) | reinterpret_cast<uintptr_t>(c.q);
+                if ((a & 15) == 0) {
+                    pcg_update_poly_f32x4_kernel<<<blocks, 256, 0, c.stream>>>(
+                        c.n, static_cast<float*>(x), static_cast<float*>(c.r), pnew, static_cast<const float*>(c.q), c.d_pcg,
+                        static_cast<double*>(c.partials), c.counter);
+                    vec = true;
+                }
+            }
+            if (!vec)
+                pcg_update_poly_kernel<P><<<blocks, 256, 0, c.stream>>>(c.n, static_cast<S*>(x), static_cast<S*>(c.r), pnew,
+                                                                        static_cast<const S*>(c.q), c.d_pcg,
+                                                                        static_cast<double*>(c.partials), c.counter);
+            PB_CUDA_TRY(cudaGetLastError());
+        }
+        pcg_precond(c, pl, dt);
+    }
+
     bool supports_pcg() const override { return P::id == PB_FP64 || P::id == PB_FP32; }
 
     static double nb(const Ctx& c, double s_words, double c_words) {

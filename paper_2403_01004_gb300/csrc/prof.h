@@ -24,13 +24,14 @@ enum KClass {
     K_PCG32_UPDATE,
     K_PCG32_REFINE,   // their right-hand-side set-up and the float64 correction x += d
     K_PTL_FULL,       // Eq. 4 over every pair of face neighbours
+    K_PCG_CHEB,       // the Chebyshev preconditioner's stencil passes
     K_NCLASS
 };
 
 inline const char* kclass_name(int k) {
     static const char* names[K_NCLASS] = {"apply", "ptl_pass", "y0_stage1", "ptl_finalize", "stage1", "stage",
                                           "pcg_init", "pcg_spmv", "pcg_update", "setup",
-                                          "pcg32_spmv", "pcg32_update", "pcg32_refine", "ptl_full"};
+                                          "pcg32_spmv", "pcg32_update", "pcg32_refine", "ptl_full", "pcg_cheb"};
     return names[k];
 }
 

@@ -112,7 +112,7 @@ __global__ void tc_coef_box_kernel(TCArgs a) {
 // Row of A at a cell from its 8 corners: A = -sum_c g_c g_c^T, g_c(p) = sigma(p) . ahat_c.
 // Writes diag(A) and the block maximum of w sum_j |A_ij| (the Gershgorin bound of L).
 __global__ void __launch_bounds__(256) tc_rows_kernel(int nr, int nt, int np, int periodic, const Coef4<double>* rec,
-                                                      double* adiag, double* part) {
+                                                      double* adiag, double* rowsum, double* part) {
     const long long n = (long long)nr * nt * np;
     const long long pl = (long long)nr * nt;
     double gmax = 0.0;
@@ -152,6 +152,7 @@ __global__ void __launch_bounds__(256) tc_rows_kernel(int nr, int nt, int np, in
 #pragma unroll
         for (int o = 0; o < 27; ++o) s += fabs(acc[o]);
         adiag[t] = acc[13];
+        rowsum[t] = s;
         gmax = fmax(gmax, rec[t].w * s);
     }
     gmax = warp_max(gmax);
@@ -254,7 +255,7 @@ __global__ void visc_coef_box_kernel(ViscArgs a) {
 
 // diag(A) = -sum of the six face coefficients; Gershgorin bound of L = 2 w sum_f c_f.
 __global__ void __launch_bounds__(256) visc_rows_kernel(int nr, int nt, int np, int periodic, const Coef4<double>* rec,
-                                                        double* adiag, double* part) {
+                                                        double* adiag, double* rowsum, double* part) {
     const long long n = (long long)nr * nt * np;
     const long long pl = (long long)nr * nt;
     double gmax = 0.0;
@@ -271,6 +272,7 @@ __global__ void __launch_bounds__(256) visc_rows_kernel(int nr, int nt, int np, 
         else if (periodic) s += rec[t + (long long)(nt - 1) * nr].b;
         s += rec[(long long)((k + np - 1) % np) * pl + (t - (long long)k * pl)].c;
         adiag[t] = -s;
+        rowsum[t] = 2.0 * s;
         gmax = fmax(gmax, 2.0 * c.w * s);
     }
     gmax = warp_max(gmax);
@@ -362,7 +364,7 @@ void setup_tc(Ctx& c, const pb_operator& op, Coef4<double>* rec, double* dt_e, b
     round_records(c, rec, n);
     double* part = static_cast<double*>(c.partials);
     double* adiag = c.s64;   // kappa is no longer needed
-    tc_rows_kernel<<<blocks, 256, 0, c.stream>>>(c.nr, c.nt, c.np, box ? 1 : 0, rec, adiag, part);
+    tc_rows_kernel<<<blocks, 256, 0, c.stream>>>(c.nr, c.nt, c.np, box ? 1 : 0, rec, adiag, c.arow, part);
     max_finalize_kernel<<<1, 256, 0, c.stream>>>(part, blocks, c.d_scalar);
     PB_CUDA_TRY(cudaGetLastError());
     PB_CUDA_TRY(cudaMemcpyAsync(c.h_scalar, c.d_scalar, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
@@ -389,7 +391,7 @@ void setup_visc(Ctx& c, const pb_operator& op, Coef4<double>* rec, double* dt_e)
         const long long n = (long long)cg.nr * cg.nt * cg.np;
         const int blocks = setup_blocks(c, n);
         visc_rows_kernel<<<blocks, 256, 0, c.stream>>>(cg.nr, cg.nt, cg.np, cg.periodic, rec + cg.offset,
-                                                       adiag + cg.offset, part + total_blocks);
+                                                       adiag + cg.offset, c.arow + cg.offset, part + total_blocks);
         total_blocks += blocks;
     }
     max_finalize_kernel<<<1, 256, 0, c.stream>>>(part, total_blocks, c.d_scalar);

@@ -47,7 +47,8 @@ def test_struct_layouts_match_header(tmp_path):
         "pb_operator": ("PbOperator", ["kind", "C", "T0", "n", "B", "rho", "nu"]),
         "pb_advance_opts": ("PbAdvanceOpts", ["scheme", "use_ptl", "max_cycles", "ptl_floor", "dt_cycles",
                                               "n_forced", "rtol", "max_iter", "fixed_iters", "check_every",
-                                              "judge_guess", "mixed_precision", "inner_rtol"]),
+                                              "judge_guess", "mixed_precision", "inner_rtol", "ptl_mode",
+                                              "precond", "pc_degree"]),
         "pb_train_opts": ("PbTrainOpts", ["steps", "batch", "crop", "border", "lr", "seed"]),
         "pb_tune": ("PbTune", ["kchunk", "blocks_per_sm", "small_tiles"]),
         "pb_kernel_stat": ("PbKernelStat", ["name", "launches", "timed_launches", "total_ms", "bytes"]),
