@@ -516,19 +516,50 @@ def batched_probe(pb, torch, reps=3):
             "speedup_vs_separate": ms_s / ms_b, "unit": UNIT}
 
 
+def learned_training_data(pb, torch, n_samples: int, shape=(64, 64, 64), q: float = 1.05, ratio: float = 1e4,
+                          seed: int = 7, rtol: float = 1e-10):
+    """Training samples for the learned guess, made by the library: Backward Euler solves (mixed
+    precision PCG to rtol) of seeded random conduction profiles on an n_r x n_theta x n_phi shell,
+    each giving the network's features of the pre-step state and the target (x - u^n)/S smoothed
+    as learned_guess smooths the network output.  Returns (feats (N, n_phi, n_theta, n_r, 16) bf16,
+    targets (N, n_phi, n_theta, n_r) f32, total PCG iterations of the solves)."""
+    import synth
+    from synth import device
+    n_r, n_t, n_p = shape
+    g = synth.make_grid(n_r, n_t, n_p, q)
+    feats = torch.empty((n_samples, n_p, n_t, n_r, 16), dtype=torch.bfloat16, device="cuda")
+    targets = torch.empty((n_samples, n_p, n_t, n_r), dtype=torch.float32, device="cuda")
+    iters = 0
+    for i in range(n_samples):
+        inp = synth.tc_random_inputs(g, seed * 100003 + i)
+        ctx = pb.parabolic_setup(g.r_face, g.t_face, g.n_phi, "tc", device.tc_fields(inp), "fp64")
+        u = torch.from_numpy(inp.T.reshape(-1)).cuda()
+        dt = ratio * pb.parabolic_dt_explicit(ctx)
+        x = u.clone()
+        st = pb.be_pcg_advance(ctx, x, dt, use_ptl=False, rtol=rtol, mixed=True)
+        iters += st["total_iters"]
+        f, t, _ = pb.pb_guess_features(ctx, u, dt, x)
+        feats[i].copy_(f.view(n_p, n_t, n_r, 16))
+        targets[i].copy_(pb.pb_guess_smooth(t, (1, n_p, n_t, n_r)).view(n_p, n_t, n_r))
+        ctx.close()
+    return feats, targets, iters
+
+
 def learned_probe(pb, torch):
     """The learned-guess workload: BE conduction on the 192 x 192 x 384 shell at dt = 1e4 dt_E,
-    PCG (float64) to rtol 1e-10 from the zero, previous-step and learned (judged) guesses.  The
-    network is trained first on solves this library makes on 48 x 48 x 96 seeded random profiles."""
+    PCG (mixed precision) to rtol 1e-10 from the zero, previous-step and learned (raw and judged)
+    guesses.  The network is trained first on 2000 solves this library makes on 64 x 64 x 64
+    seeded random profiles (targets smoothed as the guess smooths the network output)."""
     import synth
     from paper_2403_01004_gb300 import learned
     from synth import device
+    n_train, train_shape, steps = 2000, (64, 64, 64), 6000
     t0 = time.perf_counter()
-    feats, targ, gen_iters = learned.generate(64, shape=(48, 48, 96), seed=7)
+    feats, targ, gen_iters = learned_training_data(pb, torch, n_train, shape=train_shape, seed=7)
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t0
     t0 = time.perf_counter()
-    model, loss = learned.train(feats, targ, steps=1000, batch=8, crop=24, border=4, lr=2e-3, seed=1)
+    model, loss = learned.train(feats, targ, steps=steps, batch=16, crop=24, border=4, lr=2e-3, seed=1)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del feats, targ
@@ -586,9 +617,9 @@ def learned_probe(pb, torch):
     ctx.close()
     model.close()
     return {"what": "BE + PC1 PCG (mixed precision, rtol 1e-10), 192x192x384 shell, dt = 1e4 dt_E, one solve per guess",
-            "training": {"samples": 64, "sample_grid": "48x48x96", "solve_iterations": gen_iters,
-                         "generate_s": round(t_gen, 2), "steps": 1000, "train_s": round(t_train, 2),
-                         "last_batch_loss": loss},
+            "training": {"samples": n_train, "sample_grid": "x".join(map(str, train_shape)),
+                         "solve_iterations": gen_iters, "generate_s": round(t_gen, 2), "steps": steps,
+                         "batch": 16, "crop": 24, "train_s": round(t_train, 2), "last_batch_loss": loss},
             **out}
 
 

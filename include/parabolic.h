@@ -364,8 +364,21 @@ PB_API int pb_model_grad(pb_model* model, const void* feats, const void* target,
 /* Adam training on random crops of nsamples equally sized samples (device feats / targets). */
 PB_API int pb_model_train(pb_model* model, const void* feats, const void* targets, int32_t nsamples, int32_t D,
                           int32_t H, int32_t W, const pb_train_opts* opts, double* last_loss, void* stream);
-/* x0 = u + S model(features(u, dt)) for a conduction context (float64 / float32). */
+/* x0 = u + S smooth(model(features(u, dt))) for a conduction context (float64 / float32): the
+ * network's output is passed through pb_guess_smooth_passes() passes of the filter below before it
+ * becomes the increment (PCG's initial residual weights grid-scale error by up to dt/dt_E, so
+ * only the smooth part of a prediction can shorten a solve to a tight tolerance). */
 PB_API int learned_guess(pb_ctx* ctx, pb_model* model, const void* u, double dt, void* x0);
+
+/* out = in smoothed by `passes` passes of the binomial filter (1, 2, 1)/4 along each axis of
+ * S_ x D x H x W float32 fields (W fastest; the W and H ends repeat their edge value, D wraps when
+ * wrap_d): the smoothing learned_guess applies to the network output, for preparing training
+ * targets alike.  in, out, tmp: device float32 arrays of S_ D H W elements; out may equal in, tmp
+ * must differ from both.  Runs on `stream` and returns when done. */
+PB_API int pb_guess_smooth(const void* in, void* out, void* tmp, int32_t S_, int32_t D, int32_t H, int32_t W,
+                           int32_t wrap_d, int32_t passes, void* stream);
+/* The number of passes learned_guess applies. */
+PB_API int pb_guess_smooth_passes(void);
 
 /* ---- PTL without allocation ---------------------------------------------------------------- */
 /* PTL of a state (the same result as ptl_compute) for callers that cannot allocate device

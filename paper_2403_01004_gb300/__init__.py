@@ -37,7 +37,8 @@ EXPORTS = ("pb_advance_opts_init", "pb_status_string", "pb_last_error", "parabol
            "pb_ptl_noalloc", "pb_tune_init", "pb_batch_create", "pb_batch_destroy", "pb_batch_last_error",
            "pb_batch_rkl2_advance", "pb_autotune", "pb_model_create", "pb_model_destroy", "pb_model_last_error",
            "pb_model_num_params", "pb_model_get_params", "pb_model_set_params", "pb_model_save", "pb_model_load",
-           "pb_guess_features", "pb_model_forward", "pb_model_grad", "pb_model_train", "learned_guess")
+           "pb_guess_features", "pb_model_forward", "pb_model_grad", "pb_model_train", "learned_guess",
+           "pb_guess_smooth", "pb_guess_smooth_passes")
 
 
 class PbGrid(ctypes.Structure):
@@ -149,6 +150,11 @@ def load_library(path: str = LIB_PATH):
     lib.pb_model_train.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32,
                                    POINTER(PbTrainOpts), POINTER(c_double), c_void_p]
     lib.learned_guess.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_void_p]
+    lib.pb_guess_smooth.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32,
+                                    c_void_p]
+    lib.pb_guess_smooth.restype = c_int32
+    lib.pb_guess_smooth_passes.argtypes = []
+    lib.pb_guess_smooth_passes.restype = c_int32
     for name in ("pb_model_create", "pb_model_destroy", "pb_model_num_params", "pb_model_get_params",
                  "pb_model_set_params", "pb_model_save", "pb_model_load", "pb_guess_features", "pb_model_forward",
                  "pb_model_grad", "pb_model_train", "learned_guess"):
@@ -655,3 +661,19 @@ def learned_guess(ctx: Context, model: Model, u, dt: float, x0=None):
 
 __all__ = ["Model", "pb_guess_features", "pb_model_forward", "pb_model_grad", "pb_model_train", "learned_guess", "Batch", "pb_batch_create", "pb_batch_rkl2_advance", "pb_autotune", "pb_profile_enable", "pb_profile_read", "parabolic_setup", "parabolic_update", "parabolic_dt_explicit", "parabolic_apply", "ptl_compute", "rkl2_advance",
            "be_pcg_advance", "Context", "ParabolicError", "load_library", "EXPORTS"]
+
+
+def pb_guess_smooth(x, shape, wrap_d: bool = True, passes: int | None = None, stream=None):
+    """x (float32 CUDA tensor of S x D x H x W values) smoothed as learned_guess smooths the network
+    output (passes defaults to the library's); returns a new tensor."""
+    torch = _torch()
+    if x.dtype != torch.float32:
+        raise TypeError("float32 fields")
+    lib = load_library()
+    S_, D, H, W = (int(v) for v in shape)
+    out = torch.empty_like(x)
+    tmp = torch.empty_like(x)
+    n = lib.pb_guess_smooth_passes() if passes is None else int(passes)
+    _check(lib.pb_guess_smooth(c_void_p(_ptr(x)), c_void_p(_ptr(out)), c_void_p(_ptr(tmp)), S_, D, H, W,
+                               1 if wrap_d else 0, n, c_void_p(_stream_handle(stream))))
+    return out

@@ -504,6 +504,54 @@ __global__ void moments_kernel(long long n, const typename P::S* u, const typena
     }
 }
 
+// One pass of the binomial filter (1, 2, 1)/4 along one axis of [S][D][H][W] float fields (axis 0:
+// W, r; 1: H, theta; 2: D, phi); the ends repeat their edge value (no flux through them), and phi
+// wraps when wrap_d.
+__global__ void smooth_axis_kernel(const float* __restrict__ in, float* __restrict__ out, int S_, int D, int H, int W,
+                                   int axis, int wrap_d) {
+    const long long n = (long long)S_ * D * H * W;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const int w = (int)(q % W);
+        const long long t = q / W;
+        const int h = (int)(t % H);
+        const int d = (int)((t / H) % D);
+        long long lo, hi;
+        if (axis == 0) {
+            lo = w > 0 ? q - 1 : q;
+            hi = w < W - 1 ? q + 1 : q;
+        } else if (axis == 1) {
+            lo = h > 0 ? q - W : q;
+            hi = h < H - 1 ? q + W : q;
+        } else {
+            const long long pl = (long long)H * W;
+            lo = d > 0 ? q - pl : (wrap_d ? q + (long long)(D - 1) * pl : q);
+            hi = d < D - 1 ? q + pl : (wrap_d ? q - (long long)(D - 1) * pl : q);
+        }
+        out[q] = 0.25f * (in[lo] + 2.0f * in[q] + in[hi]);
+    }
+}
+
+// `passes` passes of the filter along all three axes, in place in y (tmp: scratch of the same size)
+void smooth_field(float* y, float* tmp, int S_, int D, int H, int W, int wrap_d, int passes, cudaStream_t s) {
+    const long long n = (long long)S_ * D * H * W;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+    float* a = y;
+    float* b = tmp;
+    for (int p = 0; p < passes; ++p)
+        for (int axis = 0; axis < 3; ++axis) {
+            smooth_axis_kernel<<<blocks, 256, 0, s>>>(a, b, S_, D, H, W, axis, wrap_d);
+            std::swap(a, b);
+        }
+    if (a != y) PB_CUDA_TRY(cudaMemcpyAsync(y, a, (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    PB_CUDA_TRY(cudaGetLastError());
+}
+
+// Smoothing of the network's output before it becomes a guess: PCG's initial residual weights the
+// guess's error by S = M + dt K, i.e. grid-scale error by up to dt / dt_E, and to rtol 1e-10 the
+// iteration count grows with any rough error while a smooth, accurate increment shortens the
+// solve; the learned part is therefore asked for the smooth part of the increment only.
+constexpr int kGuessSmoothPasses = 4;
+
 // x0 = u + S y
 template <class P>
 __global__ void guess_kernel(long long n, const typename P::S* u, const float* y, double S, typename P::S* x0) {
@@ -922,6 +970,24 @@ int pb_model_train(pb_model* h, const void* feats, const void* targets, int32_t 
     });
 }
 
+int pb_guess_smooth(const void* in, void* out, void* tmp, int32_t S_, int32_t D, int32_t H, int32_t W, int32_t wrap_d,
+                    int32_t passes, void* stream) {
+    if (!in || !out || !tmp || out == tmp || in == tmp || S_ <= 0 || D <= 0 || H <= 0 || W <= 0 || passes < 0)
+        return PB_EINVAL;
+    try {
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const size_t bytes = (size_t)S_ * D * H * W * sizeof(float);
+        if (in != out) PB_CUDA_TRY(cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, s));
+        smooth_field(static_cast<float*>(out), static_cast<float*>(tmp), S_, D, H, W, wrap_d, passes, s);
+        PB_CUDA_TRY(cudaStreamSynchronize(s));
+        return PB_OK;
+    } catch (const Error& e) {
+        return e.code;
+    }
+}
+
+int pb_guess_smooth_passes(void) { return kGuessSmoothPasses; }
+
 int learned_guess(pb_ctx* hc, pb_model* hm, const void* u, double dt, void* x0) {
     if (!hc || !hm) return PB_EINVAL;
     Ctx& c = hc->c;
@@ -936,6 +1002,7 @@ int learned_guess(pb_ctx* hc, pb_model* hm, const void* u, double dt, void* x0) 
         if (c.prec == PB_FP64) features_t<PolF64>(c, u, dt, m.act[0], &S);
         else features_t<PolF32>(c, u, dt, m.act[0], &S);
         forward(m, 1, c.np, c.nt, c.nr, 1, c.stream);
+        smooth_field(m.out, m.batch_target, 1, c.np, c.nt, c.nr, 1, kGuessSmoothPasses, c.stream);
         const int blocks = reduce_blocks(c);
         if (c.prec == PB_FP64)
             guess_kernel<PolF64><<<blocks, 256, 0, c.stream>>>(pts, static_cast<const double*>(u), m.out, S, static_cast<double*>(x0));
