@@ -254,6 +254,8 @@ PB_API int rkl2_advance_relag(pb_ctx* ctx, void* u_dev, double dt, const pb_adva
  * the refinements are computed in double-float arithmetic (about 48 bits, on the float32
  * pipes), and a cycle stops only when the float64 residual meets rtol; environment
  * PB_MIXED_FP64_RESIDUAL=1 (read at each call) uses float64 residuals throughout.
+ * With mixed_precision the PTL decision is taken on a float32 view of the state (F in float32,
+ * the arg-max compared in float), as the float32 contexts take it.
  * opts->precond = PB_PC_CHEBYSHEV preconditions the PCG polynomially (with mixed_precision, the
  * float32 inner solves); stats count its PCG iterations, each of which runs pc_degree - 1 extra
  * stencil passes. */

@@ -762,7 +762,15 @@ int be_pcg_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, c
                 if (!(t_rem > 1e-12 * dt)) break;
                 if (cycle >= o.max_cycles) throw Error{PB_EMAXCYCLES, "PTL cycle count above max_cycles"};
                 if (o.use_ptl) {
-                    const PtlResult r = run_ptl(c, ops, u, want_full);
+                    PtlResult r;
+                    if (o.mixed_precision && c.prec == PB_FP64) {
+                        // mixed precision: the decision on a float32 view of the state
+                        mixed_ptl(c, u, want_full);
+                        sync(c);
+                        r = *c.h_ptl;
+                    } else {
+                        r = run_ptl(c, ops, u, want_full);
+                    }
                     if (r.nonfinite) throw Error{PB_ENONFINITE, "non-finite F in the PTL pass"};
                     dtp = r.dt_ptl;
                     dfull = r.dt_full;

@@ -77,6 +77,7 @@ Ctx& mixed_shadow(Ctx& c);
 void mixed_refresh(Ctx& c);            // the shadow's records from the current float64 ones
 void mixed_residual(Ctx& c, const void* x, const void* un, double dt);   // conduction, double-float
 void free_shadow(Ctx* s);
+void mixed_ptl(Ctx& c, const void* u, bool full);    // the PTL pass on a float32 view (result in c.h_ptl)
 // plan: Chebyshev-preconditioned inner solves (nullptr: point-Jacobi)
 long long mixed_inner(Ctx& c, void* x, double dt, double inner_rtol, long long max_iter, int check_every, int* status,
                       const ChebPlan* plan = nullptr);

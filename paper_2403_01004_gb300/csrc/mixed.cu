@@ -22,10 +22,32 @@ namespace pb {
 struct PolDF { using S = double; using C = dfloat; using A = dfloat; using E = double; using U = double;
                static constexpr int id = PB_FP64; static constexpr bool CG = false; static constexpr bool DF = false; };
 
-template <> __device__ __forceinline__ dfloat cvt<dfloat, double>(double v) {
-    const float h = __double2float_rn(v);
-    return dfloat(h, __double2float_rn(v - (double)h));
+// float64 -> double-float by integer operations on the bits (no float64 arithmetic, which GB300
+// issues at a small fraction of its float32 rate): hi = the value rounded to the nearest float,
+// lo = the remainder (an integer of at most 29 bits times 2^(e-52)) rounded to float, so hi + lo
+// carries 48 significant bits.  Values outside 2^-70 <= |v| < 2^126 (and zero, non-finite) take
+// the float64 route.
+__device__ __forceinline__ dfloat split_double(double v) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((bits >> 52) & 0x7FF) - 1023;
+    if (e < -70 || e > 125) {
+        const float h = __double2float_rn(v);
+        return dfloat(h, __double2float_rn(v - (double)h));
+    }
+    const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);   // 53-bit significand
+    unsigned long long top = m >> 29;                                         // the leading 24 bits
+    const long long rem = (long long)(m & ((1ull << 29) - 1));
+    const bool up = rem > (1ll << 28) || (rem == (1ll << 28) && (top & 1ull));
+    const long long r = up ? rem - (1ll << 29) : rem;                          // |r| <= 2^28
+    top += up ? 1ull : 0ull;                                                  // 2^24 carries into the exponent
+    const unsigned int sign = (unsigned int)(bits >> 63) << 31;
+    const float hi = __uint_as_float(sign | (((unsigned int)(e + 127) << 23) + (unsigned int)(top - (1ull << 23))));
+    const float scale = __uint_as_float((unsigned int)(e - 52 + 127) << 23);  // 2^(e-52)
+    const float lo = __fmul_rn(__ll2float_rn(sign ? -r : r), scale);
+    return dfloat(hi, lo);
 }
+
+template <> __device__ __forceinline__ dfloat cvt<dfloat, double>(double v) { return split_double(v); }
 template <> __device__ __forceinline__ Coef4<dfloat> load_coef<dfloat, dfloat>(const Coef4<dfloat>* p) {
     const float4* q = reinterpret_cast<const float4*>(p);
     const float4 x = __ldg(q), y = __ldg(q + 1);
@@ -34,16 +56,17 @@ template <> __device__ __forceinline__ Coef4<dfloat> load_coef<dfloat, dfloat>(c
 
 namespace {
 
-// r = b - S x = M (u^n - x) + dt A x for the outer test of mixed-precision BE, with A x from the
-// double-float march and the rest in float64, and the sums <r, r>, <b, b>; the last block
-// writes the outer scalar state (as the float64 set-up pass does, without D^-1 and <r, D^-1 r>,
-// which the float32 inner solves form themselves).
+// r = b - S x = M (u^n - x) + dt A x for the outer test of mixed-precision BE, in double-float
+// (x, u^n split by integer operations, A x from the double-float march), and the sums <r, r>,
+// <b, b> over the leading floats (the stopping test needs a few digits of them, and a stop is
+// confirmed on the float64 residual); the last block writes the outer scalar state (as the
+// float64 set-up pass does, without D^-1 and <r, D^-1 r>, which the float32 inner solves form
+// themselves).  r is stored as its leading float (the inner solve's right-hand side is float32).
 struct EpiResidualDF {
-    struct Pre { double un, x; };
+    struct Pre { double un; };
     const double* un;
-    const double* x;
     double* r;
-    double dt;
+    dfloat dt;
     PcgScalars* sc;
     double* part;
     unsigned int* counter;
@@ -51,14 +74,15 @@ struct EpiResidualDF {
     double acc[2];
     __device__ void init() { acc[0] = acc[1] = 0.0; }
     __device__ bool skip() const { return false; }
-    __device__ Pre prefetch(long long idx) const { return Pre{__ldg(un + idx), __ldg(x + idx)}; }
-    __device__ void apply(long long idx, dfloat Au, dfloat m, dfloat, const Pre& p) {
-        const double md = to_double(m);
-        const double rv = md * (p.un - p.x) + dt * to_double(Au);
-        r[idx] = rv;
-        const double b = md * p.un;
-        acc[0] += rv * rv;
-        acc[1] += b * b;
+    __device__ Pre prefetch(long long idx) const { return Pre{__ldg(un + idx)}; }
+    // x: the marched field at this point, split exactly as its halo copies are
+    __device__ void apply(long long idx, dfloat Au, dfloat m, dfloat x, const Pre& p) {
+        const dfloat und = split_double(p.un);
+        const dfloat rv = m * (und - x) + dt * Au;
+        r[idx] = (double)rv.hi;
+        const dfloat b = m * und;
+        acc[0] += (double)rv.hi * (double)rv.hi;
+        acc[1] += (double)b.hi * (double)b.hi;
     }
     __device__ void finish() {
         block_sum<2>(acc);
@@ -151,6 +175,11 @@ init_rhs_kernel(long long n, const double* rhs, const Coef4<float>* rec_be, cons
     }
 }
 
+__global__ void to_float_kernel(long long n, const double* x, float* y) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        y[t] = __double2float_rn(x[t]);
+}
+
 __global__ void add_correction_kernel(long long n, double* x, const float* d) {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
         x[t] += (double)d[t];
@@ -226,6 +255,32 @@ Ctx& mixed_shadow(Ctx& c) {
     return *s;
 }
 
+// The PTL pass of a mixed-precision Backward Euler cycle on a float32 view of the state (as the
+// float32 super-time-stepping path takes it): F = L u in float32 on the shadow's records, the
+// arg-max compared in float, Eq. 5 from the float values; the result lands in the context's
+// mapped PTL record.  GB300 runs the float64 pass on its thin float64 pipes.
+void mixed_ptl(Ctx& c, const void* u, bool full) {
+    Ctx& s = mixed_shadow(c);
+    s.d_flag = c.d_flag;
+    s.d_ptl = c.d_ptl;
+    float* u32 = static_cast<float*>(s.r);       // free until the solve's set-up
+    {
+        KScope ks(c.prof, c.stream, K_PCG32_REFINE, (double)c.n * (8 + 4));
+        to_float_kernel<<<reduce_blocks(c), 256, 0, c.stream>>>(c.n, static_cast<const double*>(u), u32);
+        PB_CUDA_TRY(cudaGetLastError());
+    }
+    Ops* ops = ops_f32();
+    s.prof.on = c.prof.on;
+    ops->y0_pass(s, u32, s.y0, true, nullptr, 0.0);
+    ops->ptl_finalize(s, u32, s.y0);
+    if (full) ops->ptl_full(s, u32, s.y0);
+    PB_CUDA_TRY(cudaStreamSynchronize(s.stream));
+    s.prof.harvest();
+    c.prof.absorb(s.prof, K_PTL_PASS, K_PTL_PASS);
+    c.prof.absorb(s.prof, K_PTL_FINAL, K_PTL_FINAL);
+    c.prof.absorb(s.prof, K_PTL_FULL, K_PTL_FULL);
+}
+
 // Rewrites the shadow's records after every coefficient update (parabolic_update).
 void mixed_refresh(Ctx& c) {
     if (c.shadow) refresh_shadow(c, *c.shadow);
@@ -238,10 +293,11 @@ void mixed_residual(Ctx& c, const void* x, const void* un, double dt) {
     Ctx& s = mixed_shadow(c);
     if (!s.coef64) throw Error{PB_ENOTSUP, "the double-float residual is built for conduction"};
     const Coef4<dfloat>* rec = reinterpret_cast<const Coef4<dfloat>*>(s.coef64);
-    EpiResidualDF ep{static_cast<const double*>(un), static_cast<const double*>(x), static_cast<double*>(c.r), dt,
+    const float dth = (float)dt;
+    EpiResidualDF ep{static_cast<const double*>(un), static_cast<double*>(c.r), dfloat(dth, (float)(dt - (double)dth)),
                      c.d_pcg, static_cast<double*>(c.partials), c.counter, c.grid.nblocks, {0.0, 0.0}};
     const LoadState<PolDF> ld{static_cast<const double*>(x)};
-    KScope ks(c.prof, c.stream, K_PCG_INIT, (double)c.n * (8 + 8 + 32 + 8));
+    KScope ks(c.prof, c.stream, K_PCG_INIT, (double)c.n * (8 + 8 + 32 + 8));   // x, u^n, records; r
     if (c.grid.c[0].periodic)
         residual_df_kernel<true><<<c.grid.nblocks, dim3(TX, TY), 0, c.stream>>>(c.grid, rec, ld, ep);
     else
