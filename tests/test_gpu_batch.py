@@ -77,3 +77,73 @@ def test_autotune_keeps_states_and_result():
     for p, (g, inp, op, _, dt) in enumerate(probs):
         uo, _ = sts_advance(op, u_in[p], dt, "rkl2", use_ptl=False)
         assert rel_l2(to_host(us[p]), uo) <= TOL["fp32"]
+
+
+def _config2(n=64):
+    """The batched workload's problems (synth.batched_problems): grids from 16^3 to 128 x 128 x
+    256, dt/dt_E log-uniform in [10, 1e4], tilted dipoles."""
+    import synth
+    from oracle.geometry import Shell
+    from oracle.tc import TCOperator
+    out = []
+    for pr in synth.batched_problems()[:n]:
+        g = synth.make_grid(pr["n_r"], pr["n_t"], pr["n_p"], pr["q"])
+        inp = synth.tc_inputs(g, pr["seed"], m=pr["m"])
+        out.append((pr, g, inp))
+    return out
+
+
+def test_config2_batched_equals_single_problem_bit_for_bit(monkeypatch):
+    """All 64 problems of the batched workload in one launch with the 32 x 8 register tile
+    (small_tiles = 0) against each problem advanced alone by the one-problem register-tile kernel
+    (PB_DISABLE_TMA=1): the same tile arithmetic and the same stage coefficients, so the states
+    agree bit for bit.  The phi chunking differs (the batch's kchunk) and must not matter."""
+    import paper_2403_01004_gb300 as pb
+    from synth import device
+    import torch
+    probs = _config2()
+    ctxs = [pb.parabolic_setup(g.r_face, g.t_face, g.n_phi, "tc", device.tc_fields(inp), "fp32") for _, g, inp in probs]
+    u0 = [torch.from_numpy(inp.T.reshape(-1)).to("cuda", torch.float32) for _, _, inp in probs]
+    dts = [pr["ratio"] * pb.parabolic_dt_explicit(c) for (pr, _, _), c in zip(probs, ctxs)]
+    us = [u.clone() for u in u0]
+    batch = pb.pb_batch_create(ctxs, tune=dict(kchunk=8, blocks_per_sm=4, small_tiles=0))
+    st = pb.pb_batch_rkl2_advance(batch, us, dts)
+    monkeypatch.setenv("PB_DISABLE_TMA", "1")
+    for p, ((pr, g, inp), dt) in enumerate(zip(probs, dts)):
+        ctx = pb.parabolic_setup(g.r_face, g.t_face, g.n_phi, "tc", device.tc_fields(inp), "fp32")
+        x = u0[p].clone()
+        s1 = pb.rkl2_advance(ctx, x, dt, use_ptl=False)
+        assert s1["total_stages"] == st[p]["total_stages"]
+        assert torch.equal(x, us[p]), (p, pr["n_r"], pr["n_t"], pr["n_p"], float((x - us[p]).abs().max()))
+        ctx.close()
+    stages = [x["total_stages"] for x in st]
+    assert min(stages) <= 10 and max(stages) >= 150        # the workload's spread of stage counts
+
+
+def test_config2_batched_against_the_oracle():
+    """The batched workload in its tuned launch (small tiles included) against the oracle on every
+    problem small enough for it (points x stages <= 4e6): each within the float32 tolerance."""
+    import paper_2403_01004_gb300 as pb
+    from oracle.geometry import Shell
+    from oracle.tc import TCOperator
+    from synth import device
+    import torch
+    probs = _config2()
+    ctxs = [pb.parabolic_setup(g.r_face, g.t_face, g.n_phi, "tc", device.tc_fields(inp), "fp32") for _, g, inp in probs]
+    us = [torch.from_numpy(inp.T.reshape(-1)).to("cuda", torch.float32) for _, _, inp in probs]
+    u_in = [u.to(torch.float64).cpu().numpy() for u in us]
+    dts = [pr["ratio"] * pb.parabolic_dt_explicit(c) for (pr, _, _), c in zip(probs, ctxs)]
+    batch = pb.pb_batch_create(ctxs)
+    st = pb.pb_batch_rkl2_advance(batch, us, dts)
+    checked = 0
+    for p, (pr, g, inp) in enumerate(probs):
+        n = g.n_r * g.n_theta * g.n_phi
+        if n * st[p]["total_stages"] > 4e6:
+            continue
+        op = TCOperator.spherical(Shell(g.r_face, g.t_face, g.n_phi), inp.T, inp.n, inp.B)
+        uo, log = sts_advance(op, u_in[p], dts[p], "rkl2", use_ptl=False)
+        assert log.s[0] == st[p]["total_stages"]
+        got = us[p].to(torch.float64).cpu().numpy()
+        assert rel_l2(got, uo) <= TOL["fp32"], (p, rel_l2(got, uo))
+        checked += 1
+    assert checked >= 8
