@@ -187,18 +187,18 @@ tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* 
         }
         __syncthreads();
     };
-    auto U = [&](int q, int yy, int xx) -> A {
-        return cvt<A>(reinterpret_cast<const typename Field::FT*>(slot(q) + L::FIELD_OFF)[yy * L::BXW + xx]);
-    };
-    // corner (ci, cj) of plane z = k0-1+q from field slots q (plane z) and q+1 (plane z+1)
-    auto corner = [&](int cbuf, int q, int ci, int cj) -> A {
-        const C* cr = reinterpret_cast<const C*>(slot(q) + L::C_OFF) + 4 * (cj * L::CBX + ci + L::CSHIFT);
+    using FT = typename Field::FT;
+    auto field = [&](int q) -> const FT* { return reinterpret_cast<const FT*>(slot(q) + L::FIELD_OFF); };
+    // corner (ci, cj) of plane z = k0-1+q from the field of planes z (f0) and z+1 (f1) and the
+    // records of slot q (cr0)
+    auto corner = [&](int cbuf, const FT* f0, const FT* f1, const C* cr0, int ci, int cj) -> A {
+        const C* cr = cr0 + 4 * (cj * L::CBX + ci + L::CSHIFT);
         const A ca = cvt<A>(cr[0]), cb = cvt<A>(cr[1]), cc = cvt<A>(cr[2]), cw = cvt<A>(cr[3]);
-        const int x0 = ci - 1 + L::HX;
-        const A u000 = U(q, cj, x0), u100 = U(q, cj, x0 + 1);
-        const A u010 = U(q, cj + 1, x0), u110 = U(q, cj + 1, x0 + 1);
-        const A u001 = U(q + 1, cj, x0), u101 = U(q + 1, cj, x0 + 1);
-        const A u011 = U(q + 1, cj + 1, x0), u111 = U(q + 1, cj + 1, x0 + 1);
+        const int o = cj * L::BXW + ci - 1 + L::HX;
+        const A u000 = cvt<A>(f0[o]), u100 = cvt<A>(f0[o + 1]);
+        const A u010 = cvt<A>(f0[o + L::BXW]), u110 = cvt<A>(f0[o + L::BXW + 1]);
+        const A u001 = cvt<A>(f1[o]), u101 = cvt<A>(f1[o + 1]);
+        const A u011 = cvt<A>(f1[o + L::BXW]), u111 = cvt<A>(f1[o + L::BXW + 1]);
         const A P00 = u001 + u000, M00 = u001 - u000;
         const A P10 = u101 + u100, M10 = u101 - u100;
         const A P01 = u011 + u010, M01 = u011 - u010;
@@ -215,9 +215,6 @@ tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* 
         cp[3 * (TY + 1) * L::CW] = t2 - Qp;
         return cw;
     };
-    auto E = [&](int cbuf, int e, int cj, int ci) -> A {
-        return corn[cbuf * 4 * (TY + 1) * L::CW + e * (TY + 1) * L::CW + cj * L::CW + ci];
-    };
 
     if (tid == 0) {
         *abort_flag = 0;
@@ -230,10 +227,11 @@ tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* 
         for (; issued < kSlots && issued < nplanes; ++issued) issue(issued);
     issued = min(kSlots, nplanes);
 
+    auto recs = [&](int q) -> const C* { return reinterpret_cast<const C*>(slot(q) + L::C_OFF); };
     // corner plane k0-1 from slots 0 and 1
     if (!wait(0) || !wait(1)) { bail(issued, 0); return; }
-    corner(0, 0, tx + 1, ty + 1);
-    if (xci >= 0) corner(0, 0, xci, xcj);
+    corner(0, field(0), field(1), recs(0), tx + 1, ty + 1);
+    if (xci >= 0) corner(0, field(0), field(1), recs(0), xci, xcj);
     __syncthreads();
     if (tid == 0 && issued < nplanes) issue(issued);
     if (issued < nplanes) ++issued;
@@ -242,8 +240,11 @@ tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* 
     for (int k = t.k0; k < t.k1; ++k) {
         const int q = k - t.k0 + 1;
         if (!wait(q + 1)) { bail(issued, q + 1); return; }
-        const A w = corner(kb ^ 1, q, tx + 1, ty + 1);
-        if (xci >= 0) corner(kb ^ 1, q, xci, xcj);
+        const FT* f0 = field(q);
+        const FT* f1 = field(q + 1);
+        const C* cr0 = recs(q);
+        const A w = corner(kb ^ 1, f0, f1, cr0, tx + 1, ty + 1);
+        if (xci >= 0) corner(kb ^ 1, f0, f1, cr0, xci, xcj);
         // the centre and the point operands go to the epilogue at the stage-recurrence precision E
         using R = typename P::E;
         const R center = Field::CENTER_RAW
@@ -259,8 +260,12 @@ tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* 
         if (tid == 0 && issued < nplanes) issue(issued);
         if (issued < nplanes) ++issued;
         if (own) {
-            const A sum = (E(kb, 0, ty, tx) - E(kb ^ 1, 0, ty + 1, tx + 1)) + (E(kb ^ 1, 1, ty, tx) - E(kb, 1, ty + 1, tx + 1))
-                        + (E(kb, 2, ty + 1, tx) - E(kb ^ 1, 2, ty, tx + 1)) + (E(kb ^ 1, 3, ty + 1, tx) - E(kb, 3, ty, tx + 1));
+            // the eight corners of the cell: planes k-1/2 (buffer kb) and k+1/2 (kb ^ 1)
+            constexpr int EP = (TY + 1) * L::CW;          // stride between the four quad entries
+            const A* cp = corn + kb * 4 * EP + ty * L::CW + tx;
+            const A* cc = corn + (kb ^ 1) * 4 * EP + ty * L::CW + tx;
+            const A sum = (cp[0 * EP] - cc[0 * EP + L::CW + 1]) + (cc[1 * EP] - cp[1 * EP + L::CW + 1])
+                        + (cp[2 * EP + L::CW] - cc[2 * EP + 1]) + (cc[3 * EP + L::CW] - cp[3 * EP + 1]);
             const long long idx = cg.offset + (long long)k * plane + (long long)j * nr + i;
             ep.apply_c(idx, -sum, w, center, c0, c1, c2);
         }
