@@ -8,7 +8,11 @@
 // all tiles of (p, L-1) are done; those items have lower indices, so they were claimed earlier
 // by blocks that are running, and the wait cannot deadlock whatever the number of resident
 // blocks.  Each wait is bounded: on timeout the kernel raises an error flag and stops claiming.
-// Operands produced inside the launch are read through L2 (PolF32CG).
+// Operands produced inside the launch are read through L2 (PolF32CG on the register tile).
+// Problems whose arrays tensor maps can describe march their 32 x 8 tiles through the same TMA
+// ring as the one-problem kernel (tma_march_tile), with the problem's tensor maps in global
+// memory; a block acquires a level's completion, then orders its later TMA reads after it with
+// a proxy fence.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -18,6 +22,7 @@
 #include "epilogues.cuh"
 #include "launch.h"
 #include "march.cuh"
+#include "march_tma.cuh"
 #include "sts_coeffs.h"
 
 namespace pb {
@@ -33,7 +38,13 @@ struct BatchProblem {
     int tiles;                 // tiles per level
     int variant;               // 0: 32 x 8 tiles, 1: 16 x 16 tiles
     int coef_off;              // first level-coefficient record of this problem
+    const CUtensorMap* maps;   // kMaps tensor maps of the TMA ring (variant 0), or null
 };
+
+// Tensor maps of one problem: halo boxes of the fields a level marches (u, y0, buf[0..2]), point
+// boxes of the same arrays (epilogue operands), and the records.
+enum { kMapField = 0, kMapCen = 5, kMapCoef = 10, kMaps = 11 };
+using BatchTma3 = TmaLayout<PolF32, 3, PlainField<PolF32>>;   // the largest ring layout an item uses
 
 struct BatchSeg { long long begin; int p; int level; };
 
@@ -69,6 +80,52 @@ union BatchSmem {
     TileSmem<PolF32CG, 32, 8> a;
     TileSmem<PolF32CG, 16, 16> b;
 };
+
+// dynamic shared memory of a batch block: the register tiles or the largest TMA ring (+ alignment)
+constexpr int kBatchSmem = (int)sizeof(BatchSmem) > BatchTma3::TOTAL + 128 ? (int)sizeof(BatchSmem) : BatchTma3::TOTAL + 128;
+
+// Array index a (0 u, 1 y0, 2..4 buf[0..2]) of the maps
+__device__ __forceinline__ TmaRefs batch_refs(const CUtensorMap* M, int field, int c0, int c1, int c2) {
+    return TmaRefs{{M + kMapField + field, nullptr, nullptr},
+                   M + kMapCoef,
+                   {c0 >= 0 ? M + kMapCen + c0 : nullptr, c1 >= 0 ? M + kMapCen + c1 : nullptr,
+                    c2 >= 0 ? M + kMapCen + c2 : nullptr}};
+}
+
+// One work item through the TMA ring (32 x 8 tiles); the same epilogues as run_item, on the
+// one-problem kernel's policy, so a problem's stages equal its one-problem TMA launches bit for
+// bit.  Returns false when a copy never landed.
+__device__ bool run_item_tma(const BatchProblem& pr, int L, int t, const LevelCoef* lc, unsigned char* smem, int tid,
+                             int* err) {
+    using P = PolF32;
+    const TileIdx ti = tile_of<32, 8>(pr.cg, t);
+    const bool last = L == pr.s;
+    const CUtensorMap* M = pr.maps;
+    const PlainField<P> fld{};
+    if (L == 1) {
+        EpiF<P, false, false> ep{pr.y0, nullptr, 0.f, nullptr, nullptr};
+        ep.init();
+        return tma_march_tile<P>(pr.cg, ti, batch_refs(M, 0, -1, -1, -1), ep, fld, err, smem, tid);
+    }
+    if (L == 2) {
+        const LevelCoef c = lc[pr.coef_off + 2];
+        if (last) {
+            EpiStage2<P, true> ep{pr.u, nullptr, pr.u, c.a, c.b, c.c, nullptr, c.al, c.bl, c.cl};
+            return tma_march_tile<P>(pr.cg, ti, batch_refs(M, 1, 0, -1, -1), ep, fld, err, smem, tid);
+        }
+        EpiStage2<P, false> ep{nullptr, pr.buf[0], pr.buf[1], c.a, c.b, c.c, nullptr, c.al, c.bl, c.cl};
+        return tma_march_tile<P>(pr.cg, ti, batch_refs(M, 1, -1, -1, -1), ep, fld, err, smem, tid);
+    }
+    const LevelCoef c = lc[pr.coef_off + L];
+    const int bm1 = (L - 2) % 3, bm2 = (L - 3) % 3;        // buffers of d_{L-1}, d_{L-2}
+    if (last) {
+        EpiStage<P, true, true> ep{pr.buf[bm2], pr.y0, pr.u, pr.u, c.a, c.b, c.c, c.d, nullptr, c.al, c.bl, c.cl, c.dl};
+        return tma_march_tile<P>(pr.cg, ti, batch_refs(M, 2 + bm1, 1, 2 + bm2, 0), ep, fld, err, smem, tid);
+    }
+    EpiStage<P, true, false> ep{pr.buf[bm2], pr.y0, nullptr, pr.buf[(L - 1) % 3], c.a, c.b, c.c, c.d, nullptr, c.al, c.bl,
+                                c.cl, c.dl};
+    return tma_march_tile<P>(pr.cg, ti, batch_refs(M, 2 + bm1, 1, 2 + bm2, -1), ep, fld, err, smem, tid);
+}
 
 template <int TXv, int TYv>
 __device__ void run_item(const BatchProblem& pr, int L, int t, const LevelCoef* lc, TileSmem<PolF32CG, TXv, TYv>& sm,
@@ -110,7 +167,9 @@ __device__ void run_item(const BatchProblem& pr, int L, int t, const LevelCoef* 
 __global__ void __launch_bounds__(NTHREADS, 5)
 batch_kernel(const BatchProblem* __restrict__ probs, const BatchSeg* __restrict__ segs, int nsegs, long long total,
              const LevelCoef* __restrict__ lc, unsigned long long* next, int* err) {
-    __shared__ BatchSmem sm;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    BatchSmem& sm = *reinterpret_cast<BatchSmem*>(smem);
     __shared__ long long item;
     __shared__ int stop;
     const int tid = threadIdx.x;
@@ -144,14 +203,24 @@ batch_kernel(const BatchProblem* __restrict__ probs, const BatchSeg* __restrict_
             }
             __threadfence();
         }
+        // the TMA reads of this item (issued by thread 0) come after what it acquired above
+        if (tid == 0 && pr.maps) fence_proxy_async_global();
         __syncthreads();
         if (stop) return;
         const int t = (int)(it - sg.begin);
-        if (pr.variant == 0) run_item<32, 8>(pr, L, t, lc, sm.a, tid);
-        else run_item<16, 16>(pr, L, t, lc, sm.b, tid);
+        if (pr.maps) {
+            if (!run_item_tma(pr, L, t, lc, smem, tid, err)) return;
+        } else if (pr.variant == 0) {
+            run_item<32, 8>(pr, L, t, lc, sm.a, tid);
+        } else {
+            run_item<16, 16>(pr, L, t, lc, sm.b, tid);
+        }
         __threadfence();
         __syncthreads();
-        if (tid == 0) atomicAdd(&pr.done[L], 1u);
+        if (tid == 0) {
+            fence_proxy_async_global();
+            atomicAdd(&pr.done[L], 1u);
+        }
     }
 }
 
@@ -201,6 +270,7 @@ struct pb_batch {
     BatchProblem* d_probs = nullptr; size_t cap_probs = 0;
     BatchSeg* d_segs = nullptr; size_t cap_segs = 0;
     LevelCoef* d_lc = nullptr; size_t cap_lc = 0;
+    CUtensorMap* d_maps = nullptr; size_t cap_maps = 0;
     unsigned int* d_done = nullptr; size_t cap_done = 0;
     unsigned long long* d_next = nullptr;
     int* d_err = nullptr;
@@ -208,6 +278,7 @@ struct pb_batch {
     BatchProblem* h_probs = nullptr; size_t hcap_probs = 0;
     BatchSeg* h_segs = nullptr; size_t hcap_segs = 0;
     LevelCoef* h_lc = nullptr; size_t hcap_lc = 0;
+    CUtensorMap* h_maps = nullptr; size_t hcap_maps = 0;
     int* h_err = nullptr;
     // the captured launch and the structure it was captured for
     cudaGraphExec_t exec = nullptr;
@@ -225,10 +296,10 @@ void free_batch(pb_batch* b) {
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->stream) cudaStreamDestroy(b->stream);
-    void* d[] = {b->d_probs, b->d_segs, b->d_lc, b->d_done, b->d_next, b->d_err};
+    void* d[] = {b->d_probs, b->d_segs, b->d_lc, b->d_done, b->d_next, b->d_err, b->d_maps};
     for (void* p : d)
         if (p) cudaFree(p);
-    void* h[] = {b->h_probs, b->h_segs, b->h_lc, b->h_err};
+    void* h[] = {b->h_probs, b->h_segs, b->h_lc, b->h_err, b->h_maps};
     for (void* p : h)
         if (p) cudaFreeHost(p);
 }
@@ -272,6 +343,8 @@ std::vector<long long> build_tables(pb_batch* b, void* const* u, const double* d
     }
     grow(b->d_lc, b->cap_lc, lc_total);
     grow_host(b->h_lc, b->hcap_lc, lc_total);
+    grow(b->d_maps, b->cap_maps, (size_t)n * kMaps);
+    grow_host(b->h_maps, b->hcap_maps, (size_t)n * kMaps);
     grow(b->d_done, b->cap_done, done_total);
     std::vector<long long> key;
     key.push_back(b->tune.kchunk);
@@ -299,6 +372,17 @@ std::vector<long long> build_tables(pb_batch* b, void* const* u, const double* d
         pr.tiles = pr.cg.tiles_r * pr.cg.tiles_t * pr.cg.nchunk;
         pr.variant = variant;
         pr.coef_off = (int)lc_off;
+        // the TMA ring for the 32 x 8 tiles when every array can be described by a tensor map
+        pr.maps = nullptr;
+        if (variant == 0 && c.use_tma) {
+            CUtensorMap* hm = b->h_maps + (size_t)p * kMaps;
+            const void* arr[5] = {pr.u, pr.y0, pr.buf[0], pr.buf[1], pr.buf[2]};
+            bool ok = tma_coef_map(&hm[kMapCoef], pr.coef, 4, c.nr, c.nt, c.np, BatchTma3::CBX, TY + 1);
+            for (int a = 0; ok && a < 5; ++a)
+                ok = tma_state_map(&hm[kMapField + a], arr[a], 4, c.nr, c.nt, c.np, BatchTma3::BXW, TY + 2) &&
+                     tma_state_map(&hm[kMapCen + a], arr[a], 4, c.nr, c.nt, c.np, TX, TY);
+            if (ok) pr.maps = b->d_maps + (size_t)p * kMaps;
+        }
         Sts co;
         make_sts(scheme, r_of[p], co);
         const std::vector<double>&mu = co.mu, &nu = co.nu, &mut = co.mut, &gt = co.gt;
@@ -333,7 +417,8 @@ std::vector<long long> build_tables(pb_batch* b, void* const* u, const double* d
     key.push_back((long long)done_total);
     // the captured copies read these buffers: a reallocation needs a new capture
     for (const void* ptr : {(const void*)b->h_probs, (const void*)b->h_segs, (const void*)b->h_lc, (const void*)b->d_probs,
-                            (const void*)b->d_segs, (const void*)b->d_lc, (const void*)b->d_done})
+                            (const void*)b->d_segs, (const void*)b->d_lc, (const void*)b->d_done,
+                            (const void*)b->h_maps, (const void*)b->d_maps})
         key.push_back(reinterpret_cast<long long>(ptr));
     return key;
 }
@@ -350,17 +435,22 @@ void launch(pb_batch* b, void* const* u, const double* dts, int scheme, std::vec
         b->exec = nullptr;
     }
     if (!b->exec) {
+        // once per process (a function-local static: thread-safe initialisation), before capture
+        static const cudaError_t attr =
+            cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchSmem);
+        PB_CUDA_TRY(attr);
         // capture: copy the tables, clear the counters, run the persistent kernel
         cudaGraph_t graph = nullptr;
         PB_CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
         cudaMemcpyAsync(b->d_probs, b->h_probs, n * sizeof(BatchProblem), cudaMemcpyHostToDevice, b->stream);
         cudaMemcpyAsync(b->d_segs, b->h_segs, nsegs * sizeof(BatchSeg), cudaMemcpyHostToDevice, b->stream);
         cudaMemcpyAsync(b->d_lc, b->h_lc, lc_total * sizeof(LevelCoef), cudaMemcpyHostToDevice, b->stream);
+        cudaMemcpyAsync(b->d_maps, b->h_maps, n * kMaps * sizeof(CUtensorMap), cudaMemcpyHostToDevice, b->stream);
         cudaMemsetAsync(b->d_done, 0, done_total * sizeof(unsigned int), b->stream);
         cudaMemsetAsync(b->d_next, 0, sizeof(unsigned long long), b->stream);
         const int grid = std::max(1, b->tune.blocks_per_sm) * b->sm_count;
-        batch_kernel<<<grid, NTHREADS, 0, b->stream>>>(b->d_probs, b->d_segs, nsegs, total, b->d_lc, b->d_next,
-                                                       b->d_err);
+        batch_kernel<<<grid, NTHREADS, kBatchSmem, b->stream>>>(b->d_probs, b->d_segs, nsegs, total, b->d_lc,
+                                                                b->d_next, b->d_err);
         const cudaError_t le = cudaGetLastError();
         const cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
         if (le != cudaSuccess || ce != cudaSuccess)

@@ -122,30 +122,25 @@ struct TmaLayout {
     static constexpr int TOTAL = BAR_OFF + kSlots * 8 + 16;
 };
 
-template <class P, class Epi, class Field = PlainField<P>>
-__global__ void __launch_bounds__(NTHREADS)
-tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* err, Field fld = Field{}) {
+// The march of one tile t: planes [t.k0, t.k1) of its (r, theta) tile, every epilogue call made.
+// Returns false when a copy never landed (the block has recorded it in *err, drained its other
+// copies and must stop).  smem: the block's 128-byte-aligned TMA layout; tid: the linear thread
+// index (TX x TY threads).  The mbarriers are initialised on entry and invalidated on exit, so a
+// persistent block can march tile after tile.
+template <class P, class Epi, class Field>
+__device__ __forceinline__ bool tma_march_tile(const CompGrid& cg, const TileIdx& t, const TmaRefs& m, Epi& ep,
+                                               const Field& fld, int* err, unsigned char* smem, int tid) {
     using S = typename P::S;
     using C = typename P::C;
     using A = typename P::A;
     using L = TmaLayout<P, Epi::NC, Field>;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    // TMA destinations are kept 128-byte aligned (the launch adds 128 bytes of slack)
-    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
     int* abort_flag = reinterpret_cast<int*>(smem + L::BAR_OFF + kSlots * 8);
     A* corn = reinterpret_cast<A*>(smem + L::CORN_OFF);
 
-    Epi ep = ep_in;
-    ep.init();
-    if (ep.skip()) return;
-    fld.init();
-
-    const TileIdx t = decode_tile(g);
-    const CompGrid& cg = g.c[0];
     const int nr = cg.nr, nt = cg.nt, np = cg.np;
     const long long plane = (long long)nr * nt;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+    const int tx = tid % TX, ty = tid / TX;
     const int i = t.i0 + tx, j = t.j0 + ty;
     const bool own = (i < nr) && (j < nt);
     const int nplanes = t.k1 - t.k0 + 2;       // planes k0-1 .. k1
@@ -162,11 +157,11 @@ tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* 
         z = z < 0 ? z + np : (z >= np ? z - np : z);
         mbar_expect_tx(bar, L::TX_BYTES);
 #pragma unroll
-        for (int f = 0; f < Field::NF; ++f) tma_load_3d(s + L::U_OFF + f * L::U_PITCH, &maps.halo[f], t.i0 - L::HX, t.j0 - 1, z, bar);
-        if constexpr (L::CPACK) tma_load_3d(s + L::C_OFF, &maps.coef, t.i0 - 2, t.j0 - 1, z, bar);
-        else tma_load_4d(s + L::C_OFF, &maps.coef, 0, t.i0 - 1, t.j0 - 1, z, bar);
+        for (int f = 0; f < Field::NF; ++f) tma_load_3d(s + L::U_OFF + f * L::U_PITCH, m.halo[f], t.i0 - L::HX, t.j0 - 1, z, bar);
+        if constexpr (L::CPACK) tma_load_3d(s + L::C_OFF, m.coef, t.i0 - 2, t.j0 - 1, z, bar);
+        else tma_load_4d(s + L::C_OFF, m.coef, 0, t.i0 - 1, t.j0 - 1, z, bar);
 #pragma unroll
-        for (int a = 0; a < Epi::NC; ++a) tma_load_3d(s + L::E_OFF + a * align128(L::E_BYTES), &maps.cen[a], t.i0, t.j0, z, bar);
+        for (int a = 0; a < Epi::NC; ++a) tma_load_3d(s + L::E_OFF + a * align128(L::E_BYTES), m.cen[a], t.i0, t.j0, z, bar);
     };
     // all threads wait for slot q; returns false (in every thread) if the copy never landed
     auto wait = [&](int q) -> bool {
@@ -184,6 +179,7 @@ tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* 
         if (tid == 0) {
             atomicExch(err, 1);
             for (int q = waited; q < issued; ++q) mbar_wait(bars + (q % kSlots), (q / kSlots) & 1);
+            for (int b = 0; b < kSlots; ++b) mbar_inval(bars + b);
         }
         __syncthreads();
     };
@@ -229,7 +225,7 @@ tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* 
 
     auto recs = [&](int q) -> const C* { return reinterpret_cast<const C*>(slot(q) + L::C_OFF); };
     // corner plane k0-1 from slots 0 and 1
-    if (!wait(0) || !wait(1)) { bail(issued, 0); return; }
+    if (!wait(0) || !wait(1)) { bail(issued, 0); return false; }
     corner(0, field(0), field(1), recs(0), tx + 1, ty + 1);
     if (xci >= 0) corner(0, field(0), field(1), recs(0), xci, xcj);
     __syncthreads();
@@ -239,7 +235,7 @@ tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* 
     int kb = 0;
     for (int k = t.k0; k < t.k1; ++k) {
         const int q = k - t.k0 + 1;
-        if (!wait(q + 1)) { bail(issued, q + 1); return; }
+        if (!wait(q + 1)) { bail(issued, q + 1); return false; }
         const FT* f0 = field(q);
         const FT* f1 = field(q + 1);
         const C* cr0 = recs(q);
@@ -271,6 +267,24 @@ tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* 
         }
         kb ^= 1;
     }
+    // every copy issued has been waited for (the last iteration waited for the last plane)
+    if (tid == 0)
+        for (int b = 0; b < kSlots; ++b) mbar_inval(bars + b);
+    return true;
+}
+
+template <class P, class Epi, class Field = PlainField<P>>
+__global__ void __launch_bounds__(NTHREADS)
+tc_march_tma(MarchGrid g, const __grid_constant__ TmaMaps maps, Epi ep_in, int* err, Field fld = Field{}) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // TMA destinations are kept 128-byte aligned (the launch adds 128 bytes of slack)
+    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    Epi ep = ep_in;
+    ep.init();
+    if (ep.skip()) return;
+    fld.init();
+    const TmaRefs m{{&maps.halo[0], &maps.halo[1], &maps.halo[2]}, &maps.coef, {&maps.cen[0], &maps.cen[1], &maps.cen[2]}};
+    if (!tma_march_tile<P>(g.c[0], decode_tile(g), m, ep, fld, err, smem, threadIdx.x + TX * threadIdx.y)) return;
     ep.finish();
 }
 

@@ -21,6 +21,17 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
+// Returns a barrier's memory to ordinary use (required before it is initialised again).
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Orders this thread's earlier generic-proxy view of global memory (data other blocks wrote and
+// this thread has acquired) before its later async-proxy (TMA) reads.
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -62,6 +73,14 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
           "r"(smem_u32(bar))
         : "memory");
 }
+
+// Device-side references to the tensor maps one tile march reads: param-space maps of a
+// one-problem launch, or global-memory maps of the batched launch.
+struct TmaRefs {
+    const CUtensorMap* halo[3];
+    const CUtensorMap* coef;
+    const CUtensorMap* cen[3];
+};
 
 // Host: the tensor maps one TMA march launch needs (all for one scalar field grid).
 struct TmaMaps {

@@ -93,14 +93,18 @@ def _config2(n=64):
     return out
 
 
-def test_config2_batched_equals_single_problem_bit_for_bit(monkeypatch):
-    """All 64 problems of the batched workload in one launch with the 32 x 8 register tile
-    (small_tiles = 0) against each problem advanced alone by the one-problem register-tile kernel
-    (PB_DISABLE_TMA=1): the same tile arithmetic and the same stage coefficients, so the states
-    agree bit for bit.  The phi chunking differs (the batch's kchunk) and must not matter."""
+@pytest.mark.parametrize("tma", [True, False])
+def test_config2_batched_equals_single_problem_bit_for_bit(monkeypatch, tma):
+    """All 64 problems of the batched workload in one launch with the 32 x 8 tile (small_tiles = 0)
+    against each problem advanced alone by the one-problem kernel of the same tile: the TMA ring
+    (the batch marches its tiles with the same per-tile function and maps of the same boxes) or,
+    with PB_DISABLE_TMA=1 for every context, the register tile.  Same tile arithmetic and the same
+    stage coefficients, so the states agree bit for bit; the phi chunking differs (the batch's
+    kchunk) and must not matter."""
     import paper_2403_01004_gb300 as pb
     from synth import device
     import torch
+    monkeypatch.setenv("PB_DISABLE_TMA", "0" if tma else "1")
     probs = _config2()
     ctxs = [pb.parabolic_setup(g.r_face, g.t_face, g.n_phi, "tc", device.tc_fields(inp), "fp32") for _, g, inp in probs]
     u0 = [torch.from_numpy(inp.T.reshape(-1)).to("cuda", torch.float32) for _, _, inp in probs]
@@ -108,7 +112,6 @@ def test_config2_batched_equals_single_problem_bit_for_bit(monkeypatch):
     us = [u.clone() for u in u0]
     batch = pb.pb_batch_create(ctxs, tune=dict(kchunk=8, blocks_per_sm=4, small_tiles=0))
     st = pb.pb_batch_rkl2_advance(batch, us, dts)
-    monkeypatch.setenv("PB_DISABLE_TMA", "1")
     for p, ((pr, g, inp), dt) in enumerate(zip(probs, dts)):
         ctx = pb.parabolic_setup(g.r_face, g.t_face, g.n_phi, "tc", device.tc_fields(inp), "fp32")
         x = u0[p].clone()
