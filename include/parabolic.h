@@ -137,8 +137,9 @@ typedef struct {
                                  has the smaller initial residual ||b - S x||; 0 uses x0     */
     int32_t mixed_precision;  /* BE on a PB_FP64 context: 1 solves by iterative refinement --
                                  float64 residuals, float32 PCG corrections (default 0)      */
-    double inner_rtol;        /* relative residual of each float32 correction (default 1e-3;
-                                 the last correction stops once the outer test is met)      */
+    double inner_rtol;        /* relative residual of each float32 correction (default 1e-6:
+                                 two corrections reach 1e-10; the last one stops once the
+                                 outer test is met)                                         */
     int32_t ptl_mode;         /* PB_PTL_FMAX (default) or PB_PTL_FULL: the PTL value that
                                  sets each cycle                                            */
     int32_t precond;          /* BE: PB_PC_JACOBI (default, PC1) or PB_PC_CHEBYSHEV          */

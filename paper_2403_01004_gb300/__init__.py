@@ -343,7 +343,7 @@ PRECONDS = {"jacobi": 0, "chebyshev": 1}
 
 
 def _opts(scheme="rkl2", use_ptl=True, max_cycles=0, ptl_floor=1.0, forced=None, rtol=1e-10,
-          max_iter=100000, fixed_iters=0, check_every=8, judge_guess=True, mixed=False, inner_rtol=1e-3,
+          max_iter=100000, fixed_iters=0, check_every=8, judge_guess=True, mixed=False, inner_rtol=1e-6,
           ptl_mode="fmax", precond="jacobi", pc_degree=3):
     lib = load_library()
     o = PbAdvanceOpts()
@@ -450,7 +450,7 @@ def be_pcg_advance(ctx: Context, u, dt: float, use_ptl: bool = True, forced=None
                    max_iter: int = 100000, fixed_iters: int = 0, x0=None, max_cycles: int = 0,
                    ptl_floor: float = 1.0, check_every: int = 8, stats_capacity: int = 4096,
                    raise_on_error: bool = True, judge_guess: bool = True, mixed: bool = False,
-                   inner_rtol: float = 1e-3, ptl_mode: str = "fmax", record_full: bool = False,
+                   inner_rtol: float = 1e-6, ptl_mode: str = "fmax", record_full: bool = False,
                    precond: str = "jacobi", pc_degree: int = 3) -> dict:
     """Advances u in place over dt with Backward Euler + PCG under PTL cycling, preconditioned by
     point-Jacobi (precond "jacobi", PC1) or by the degree-pc_degree Chebyshev polynomial in

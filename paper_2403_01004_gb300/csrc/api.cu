@@ -157,7 +157,7 @@ pb_advance_opts resolve(const pb_advance_opts* o) {
     if (!(r.rtol > 0.0)) r.rtol = 1e-10;
     if (r.max_iter < 0) r.max_iter = 100000;
     if (r.check_every <= 0) r.check_every = 8;
-    if (!(r.inner_rtol > 0.0) || !(r.inner_rtol < 1.0)) r.inner_rtol = 1e-3;
+    if (!(r.inner_rtol > 0.0) || !(r.inner_rtol < 1.0)) r.inner_rtol = 1e-6;
     if (r.scheme != PB_RKL2 && r.scheme != PB_RKG2) throw Error{PB_EINVAL, "unknown scheme"};
     if (r.ptl_mode != PB_PTL_FMAX && r.ptl_mode != PB_PTL_FULL) throw Error{PB_EINVAL, "unknown ptl_mode"};
     if (r.precond != PB_PC_JACOBI && r.precond != PB_PC_CHEBYSHEV) throw Error{PB_EINVAL, "unknown precond"};
@@ -310,7 +310,7 @@ void pb_advance_opts_init(pb_advance_opts* o) {
     o->check_every = 8;
     o->judge_guess = 1;
     o->mixed_precision = 0;
-    o->inner_rtol = 1e-3;
+    o->inner_rtol = 1e-6;
     o->ptl_mode = PB_PTL_FMAX;
     o->precond = PB_PC_JACOBI;
     o->pc_degree = 3;

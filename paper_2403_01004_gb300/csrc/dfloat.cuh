@@ -8,10 +8,9 @@ namespace pb {
 
 // A value held as the unevaluated sum hi + lo of two floats (|lo| <= ulp(hi) / 2), about 48
 // significant bits, computed on the float32 pipes (GB300 issues float64 at a small fraction of
-// the float32 rate).  Sums follow Knuth's two-sum and Dekker's fast two-sum (the accurate
-// double-float addition); products take the exact rounding error of hi * hi from a fused
-// multiply-add.  Every operation is an explicit round-to-nearest intrinsic, so the compiler
-// neither contracts nor reorders the error terms.
+// the float32 rate).  Sums follow Knuth's two-sum and Dekker's fast two-sum; products take the
+// exact rounding error of hi * hi from a fused multiply-add.  Every operation is an explicit
+// round-to-nearest intrinsic, so the compiler neither contracts nor reorders the error terms.
 struct dfloat {
     float hi, lo;
     dfloat() = default;
@@ -29,11 +28,13 @@ __device__ __forceinline__ dfloat fast_two_sum(float a, float b) {   // |a| >= |
     const float s = __fadd_rn(a, b);
     return dfloat(s, __fsub_rn(b, __fsub_rn(s, a)));
 }
+// The sum's error is a small multiple of 2^-48 (|x| + |y|): relative to the operands, not to the
+// result (when x and y nearly cancel the result keeps the absolute, not the relative, accuracy).
+// That is the accuracy a residual of a stencil needs, whose error budget is set by the magnitude
+// of the terms it sums; the low parts are therefore added in one float (no second two-sum).
 __device__ __forceinline__ dfloat operator+(dfloat x, dfloat y) {
-    dfloat s = two_sum(x.hi, y.hi);
-    const dfloat t = two_sum(x.lo, y.lo);
-    s = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
-    return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+    const dfloat s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
 }
 __device__ __forceinline__ dfloat operator-(dfloat x) { return dfloat(-x.hi, -x.lo); }
 __device__ __forceinline__ dfloat operator-(dfloat x, dfloat y) { return x + (-y); }

@@ -43,8 +43,33 @@ __device__ __forceinline__ dfloat split_double(double v) {
     const unsigned int sign = (unsigned int)(bits >> 63) << 31;
     const float hi = __uint_as_float(sign | (((unsigned int)(e + 127) << 23) + (unsigned int)(top - (1ull << 23))));
     const float scale = __uint_as_float((unsigned int)(e - 52 + 127) << 23);  // 2^(e-52)
-    const float lo = __fmul_rn(__ll2float_rn(sign ? -r : r), scale);
+    const float lo = __fmul_rn(__int2float_rn((int)(sign ? -r : r)), scale);   // |r| <= 2^28
     return dfloat(hi, lo);
+}
+
+// float64 -> float rounded to nearest (ties to even) by integer operations on the bits; results
+// outside the normal float range (and zero, non-finite values) take the conversion instruction
+__device__ __forceinline__ float narrow(double v) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((bits >> 52) & 0x7FF) - 1023;
+    if (e < -126 || e > 126) return __double2float_rn(v);
+    const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    unsigned long long top = m >> 29;
+    const unsigned long long rem = m & ((1ull << 29) - 1);
+    if (rem > (1ull << 28) || (rem == (1ull << 28) && (top & 1ull))) ++top;   // 2^24 carries into the exponent
+    const unsigned int sign = (unsigned int)(bits >> 63) << 31;
+    return __uint_as_float(sign | (((unsigned int)(e + 127) << 23) + (unsigned int)(top - (1ull << 23))));
+}
+
+// float -> float64 by integer operations on the bits (exact; zero, subnormal and non-finite
+// values take the conversion instruction, which GB300 issues on its float64 pipes)
+__device__ __forceinline__ double widen(float f) {
+    const unsigned int b = __float_as_uint(f);
+    const unsigned int ex = (b >> 23) & 0xFFu;
+    if (ex == 0u || ex == 0xFFu) return (double)f;
+    const unsigned long long w = ((unsigned long long)(b >> 31) << 63) | ((unsigned long long)(ex + 896u) << 52) |
+                                 ((unsigned long long)(b & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)w);
 }
 
 template <> __device__ __forceinline__ dfloat cvt<dfloat, double>(double v) { return split_double(v); }
@@ -71,25 +96,26 @@ struct EpiResidualDF {
     double* part;
     unsigned int* counter;
     int nblocks;
-    double acc[2];
-    __device__ void init() { acc[0] = acc[1] = 0.0; }
+    DfAcc acc[2];      // <r, r> and <b, b> of this thread, in double-float on the float32 pipes
+    __device__ void init() { acc[0] = DfAcc{0.f, 0.f}; acc[1] = DfAcc{0.f, 0.f}; }
     __device__ bool skip() const { return false; }
     __device__ Pre prefetch(long long idx) const { return Pre{__ldg(un + idx)}; }
     // x: the marched field at this point, split exactly as its halo copies are
     __device__ void apply(long long idx, dfloat Au, dfloat m, dfloat x, const Pre& p) {
         const dfloat und = split_double(p.un);
         const dfloat rv = m * (und - x) + dt * Au;
-        r[idx] = (double)rv.hi;
+        r[idx] = widen(rv.hi);
         const dfloat b = m * und;
-        acc[0] += (double)rv.hi * (double)rv.hi;
-        acc[1] += (double)b.hi * (double)b.hi;
+        acc[0].add(rv.hi, 0.f, rv.hi);
+        acc[1].add(b.hi, 0.f, b.hi);
     }
     __device__ void finish() {
-        block_sum<2>(acc);
+        double v[2] = {(double)acc[0].s + (double)acc[0].e, (double)acc[1].s + (double)acc[1].e};
+        block_sum<2>(v);
         const int tid = threadIdx.x + blockDim.x * threadIdx.y;
         if (tid == 0) {
-            part[blockIdx.x * 4 + 0] = acc[0];
-            part[blockIdx.x * 4 + 1] = acc[1];
+            part[blockIdx.x * 4 + 0] = v[0];
+            part[blockIdx.x * 4 + 1] = v[1];
         }
         if (last_block(counter, nblocks)) {
             double v[2];
@@ -137,18 +163,22 @@ __global__ void records_df_kernel(long long n, const Coef4<double>* rec, Coef4<d
 __global__ void __launch_bounds__(256)
 init_rhs_kernel(long long n, const double* rhs, const Coef4<float>* rec_be, const float* adiag, double dt, float* r,
                 float* dinv, float* d, PcgScalars* sc, double* part, unsigned int* counter) {
-    double acc[3] = {0.0, 0.0, 0.0};
+    // the sums in double-float on the float32 pipes (GB300 issues float64 at a small fraction of
+    // the float32 rate); <rhs, rhs> from the leading float of rhs (the inner test needs a few digits)
+    DfAcc a[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    const float dtf = (float)dt;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-        const float rs = (float)rhs[t];
-        const float ds = 1.0f / (rec_be[t].w - (float)dt * adiag[t]);
+        const float rs = narrow(rhs[t]);
+        const float ds = 1.0f / (rec_be[t].w - dtf * adiag[t]);
         r[t] = rs;
         dinv[t] = ds;
         d[t] = 0.0f;
-        const double z = (double)(ds * rs);
-        acc[0] += (double)rs * z;
-        acc[1] += (double)rs * (double)rs;
-        acc[2] += rhs[t] * rhs[t];
+        a[0].add(rs, 0.f, ds * rs);
+        a[1].add(rs, 0.f, rs);
     }
+    a[2] = a[1];
+    double acc[3];
+    for (int k = 0; k < 3; ++k) acc[k] = (double)a[k].s + (double)a[k].e;
     block_sum<3>(acc);
     if (threadIdx.x == 0) {
         part[blockIdx.x * 4 + 0] = acc[0];
@@ -177,12 +207,12 @@ init_rhs_kernel(long long n, const double* rhs, const Coef4<float>* rec_be, cons
 
 __global__ void to_float_kernel(long long n, const double* x, float* y) {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
-        y[t] = __double2float_rn(x[t]);
+        y[t] = narrow(x[t]);
 }
 
 __global__ void add_correction_kernel(long long n, double* x, const float* d) {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
-        x[t] += (double)d[t];
+        x[t] += widen(d[t]);
 }
 
 // The shadow's records from the context's current float64 ones: float32 records (w and M = 1/w
@@ -295,7 +325,7 @@ void mixed_residual(Ctx& c, const void* x, const void* un, double dt) {
     const Coef4<dfloat>* rec = reinterpret_cast<const Coef4<dfloat>*>(s.coef64);
     const float dth = (float)dt;
     EpiResidualDF ep{static_cast<const double*>(un), static_cast<double*>(c.r), dfloat(dth, (float)(dt - (double)dth)),
-                     c.d_pcg, static_cast<double*>(c.partials), c.counter, c.grid.nblocks, {0.0, 0.0}};
+                     c.d_pcg, static_cast<double*>(c.partials), c.counter, c.grid.nblocks, {}};
     const LoadState<PolDF> ld{static_cast<const double*>(x)};
     KScope ks(c.prof, c.stream, K_PCG_INIT, (double)c.n * (8 + 8 + 32 + 8));   // x, u^n, records; r
     if (c.grid.c[0].periodic)
