@@ -117,7 +117,7 @@ struct TmaLayout {
     static constexpr int TX_BYTES = NF * U_BYTES + C_BYTES + NC * E_BYTES;   // bytes a slot's copies deliver
     static constexpr int CW = TX + 2;                                    // corner row pitch
     static constexpr int CORN_OFF = kSlots * SLOT;
-    static constexpr int CORN_BYTES = 2 * 4 * (TY + 1) * CW * (int)sizeof(A);
+    static constexpr int CORN_BYTES = 4 * (TY + 1) * CW * (int)sizeof(A);   // one corner plane
     static constexpr int BAR_OFF = align128(CORN_OFF + CORN_BYTES);
     static constexpr int TOTAL = BAR_OFF + kSlots * 8 + 16;
 };
@@ -187,7 +187,7 @@ __device__ __forceinline__ bool tma_march_tile(const CompGrid& cg, const TileIdx
     auto field = [&](int q) -> const FT* { return reinterpret_cast<const FT*>(slot(q) + L::FIELD_OFF); };
     // corner (ci, cj) of plane z = k0-1+q from the field of planes z (f0) and z+1 (f1) and the
     // records of slot q (cr0)
-    auto corner = [&](int cbuf, const FT* f0, const FT* f1, const C* cr0, int ci, int cj) -> A {
+    auto corner = [&](const FT* f0, const FT* f1, const C* cr0, int ci, int cj) -> A {
         const C* cr = cr0 + 4 * (cj * L::CBX + ci + L::CSHIFT);
         const A ca = cvt<A>(cr[0]), cb = cvt<A>(cr[1]), cc = cvt<A>(cr[2]), cw = cvt<A>(cr[3]);
         const int o = cj * L::BXW + ci - 1 + L::HX;
@@ -204,7 +204,7 @@ __device__ __forceinline__ bool tma_march_tile(const CompGrid& cg, const TileIdx
         const A s = ca * Dr + cb * Dt + cc * Dp;
         const A Qr = ca * s, Qt = cb * s, Qp = cc * s;
         const A t1 = Qr + Qt, t2 = Qr - Qt;
-        A* cp = corn + cbuf * 4 * (TY + 1) * L::CW + cj * L::CW + ci;
+        A* cp = corn + cj * L::CW + ci;
         cp[0 * (TY + 1) * L::CW] = t1 + Qp;
         cp[1 * (TY + 1) * L::CW] = t1 - Qp;
         cp[2 * (TY + 1) * L::CW] = t2 + Qp;
@@ -226,21 +226,30 @@ __device__ __forceinline__ bool tma_march_tile(const CompGrid& cg, const TileIdx
     auto recs = [&](int q) -> const C* { return reinterpret_cast<const C*>(slot(q) + L::C_OFF); };
     // corner plane k0-1 from slots 0 and 1
     if (!wait(0) || !wait(1)) { bail(issued, 0); return false; }
-    corner(0, field(0), field(1), recs(0), tx + 1, ty + 1);
-    if (xci >= 0) corner(0, field(0), field(1), recs(0), xci, xcj);
+    corner(field(0), field(1), recs(0), tx + 1, ty + 1);
+    if (xci >= 0) corner(field(0), field(1), recs(0), xci, xcj);
     __syncthreads();
     if (tid == 0 && issued < nplanes) issue(issued);
     if (issued < nplanes) ++issued;
 
-    int kb = 0;
+    // One corner plane lives in shared memory at a time: the entries of plane k-1/2 that the
+    // cell of plane k needs (its four low-phi corners) are kept in registers (e0..e3) from the
+    // iteration that read plane k-1/2 as its high-phi side; the barrier inside wait() orders
+    // those reads before the next plane's corners overwrite the buffer.
+    constexpr int EP = (TY + 1) * L::CW;          // stride between the four quad entries
+    const A* cb = corn + ty * L::CW + tx;
+    A e0 = A(0), e1 = A(0), e2 = A(0), e3 = A(0);
+    if (own) {
+        e0 = cb[0 * EP]; e1 = cb[1 * EP + L::CW + 1]; e2 = cb[2 * EP + L::CW]; e3 = cb[3 * EP + 1];
+    }
     for (int k = t.k0; k < t.k1; ++k) {
         const int q = k - t.k0 + 1;
         if (!wait(q + 1)) { bail(issued, q + 1); return false; }
         const FT* f0 = field(q);
         const FT* f1 = field(q + 1);
         const C* cr0 = recs(q);
-        const A w = corner(kb ^ 1, f0, f1, cr0, tx + 1, ty + 1);
-        if (xci >= 0) corner(kb ^ 1, f0, f1, cr0, xci, xcj);
+        const A w = corner(f0, f1, cr0, tx + 1, ty + 1);
+        if (xci >= 0) corner(f0, f1, cr0, xci, xcj);
         // the centre and the point operands go to the epilogue at the stage-recurrence precision E
         using R = typename P::E;
         const R center = Field::CENTER_RAW
@@ -256,16 +265,12 @@ __device__ __forceinline__ bool tma_march_tile(const CompGrid& cg, const TileIdx
         if (tid == 0 && issued < nplanes) issue(issued);
         if (issued < nplanes) ++issued;
         if (own) {
-            // the eight corners of the cell: planes k-1/2 (buffer kb) and k+1/2 (kb ^ 1)
-            constexpr int EP = (TY + 1) * L::CW;          // stride between the four quad entries
-            const A* cp = corn + kb * 4 * EP + ty * L::CW + tx;
-            const A* cc = corn + (kb ^ 1) * 4 * EP + ty * L::CW + tx;
-            const A sum = (cp[0 * EP] - cc[0 * EP + L::CW + 1]) + (cc[1 * EP] - cp[1 * EP + L::CW + 1])
-                        + (cp[2 * EP + L::CW] - cc[2 * EP + 1]) + (cc[3 * EP + L::CW] - cp[3 * EP + 1]);
+            // the eight corners of the cell: planes k-1/2 (registers) and k+1/2 (the buffer)
+            const A sum = (e0 - cb[0 * EP + L::CW + 1]) + (cb[1 * EP] - e1) + (e2 - cb[2 * EP + 1]) + (cb[3 * EP + L::CW] - e3);
+            e0 = cb[0 * EP]; e1 = cb[1 * EP + L::CW + 1]; e2 = cb[2 * EP + L::CW]; e3 = cb[3 * EP + 1];
             const long long idx = cg.offset + (long long)k * plane + (long long)j * nr + i;
             ep.apply_c(idx, -sum, w, center, c0, c1, c2);
         }
-        kb ^= 1;
     }
     // every copy issued has been waited for (the last iteration waited for the last plane)
     if (tid == 0)
