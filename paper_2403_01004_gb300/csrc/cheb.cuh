@@ -118,10 +118,10 @@ struct EpiCheb {
     unsigned int* counter;
     int nblocks;
     int done;
-    double acc[1];
+    DotAcc<A> acc;
     static constexpr int NC = KIND == 3 ? 3 : 2;
     __device__ void init() {
-        acc[0] = 0.0;
+        acc.init();
         done = sc->done;
     }
     __device__ bool skip() const { return done != 0; }
@@ -135,13 +135,14 @@ struct EpiCheb {
         const A sy = m * y - dt * Au;
         const S ys = cvt<S>(y + c1 * (y - yp) + c2 * (dv * (rv - sy)));
         out[idx] = ys;
-        if (LAST) acc[0] += (double)rv * (double)cvt<A>(ys);
+        if (LAST) acc.add(rv, cvt<A>(ys));
     }
     __device__ void finish() {
         if (!LAST) return;
-        block_sum<1>(acc);
+        double v0[1] = {acc.value()};
+        block_sum<1>(v0);
         const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-        if (tid == 0) part[blockIdx.x * 4] = acc[0];
+        if (tid == 0) part[blockIdx.x * 4] = v0[0];
         if (last_block(counter, nblocks)) {
             double v[1];
             sum_partials<1>(part, nblocks, 4, v);

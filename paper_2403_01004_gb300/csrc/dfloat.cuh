@@ -70,6 +70,24 @@ struct DfAcc {
     __device__ __forceinline__ float value() const { return __fadd_rn(s, e); }
 };
 
+// A per-thread sum of products a b read out as a double: in double-float on the float32 pipes
+// for float operands (each product exact from a fused multiply-add, the sum about 44 bits: the
+// accuracy of a float64 sum of float products, without GB300's thin float64 pipes on every
+// point), a plain float64 sum for double operands.
+template <typename A> struct DotAcc;
+template <> struct DotAcc<float> {
+    DfAcc a;
+    __device__ __forceinline__ void init() { a.s = 0.f; a.e = 0.f; }
+    __device__ __forceinline__ void add(float x, float y) { a.add(x, 0.f, y); }
+    __device__ __forceinline__ double value() const { return (double)a.s + (double)a.e; }
+};
+template <> struct DotAcc<double> {
+    double v;
+    __device__ __forceinline__ void init() { v = 0.0; }
+    __device__ __forceinline__ void add(double x, double y) { v += x * y; }
+    __device__ __forceinline__ double value() const { return v; }
+};
+
 // c v rounded once, with c = hi + lo
 __device__ __forceinline__ float df_scale(float ch, float cl, float v) {
     const float p = __fmul_rn(ch, v);

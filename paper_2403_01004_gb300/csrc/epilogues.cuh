@@ -308,10 +308,10 @@ struct EpiPcgSpmv {
     int nblocks;
     A dt;
     int done;
-    double acc[1];
+    DotAcc<A> acc;
     static constexpr int NC = 0;     // point operands delivered by the TMA kernel
     __device__ void init() {
-        acc[0] = 0.0;
+        acc.init();
         done = sc->done;
     }
     __device__ bool skip() const { return done != 0; }
@@ -323,12 +323,13 @@ struct EpiPcgSpmv {
         const S qs = cvt<S>(m * pv - dt * Au);
         pout[idx] = ps;
         q[idx] = qs;
-        acc[0] += (double)cvt<A>(ps) * (double)cvt<A>(qs);
+        acc.add(cvt<A>(ps), cvt<A>(qs));
     }
     __device__ void finish() {
-        block_sum<1>(acc);
+        double v0[1] = {acc.value()};
+        block_sum<1>(v0);
         const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-        if (tid == 0) part[blockIdx.x * 4] = acc[0];
+        if (tid == 0) part[blockIdx.x * 4] = v0[0];
         if (last_block(counter, nblocks)) {
             double v[1];
             sum_partials<1>(part, nblocks, 4, v);

@@ -148,7 +148,7 @@ class OpsImpl : public Ops {
         const S* yprev = static_cast<const S*>(c.cheb[1 + (j - 1) % 2]);   // y_{j-1} (j >= 3)
         EpiCheb<P, KIND, LAST> ep{r, dinv, KIND == 3 ? yprev : nullptr, out, (A)dt, (A)pl.c1[j], (A)pl.c2[j],
                                   (A)pl.inv_theta, c.d_pcg, static_cast<double*>(c.partials), c.counter,
-                                  c.grid.nblocks, 0, {0.0}};
+                                  c.grid.nblocks, 0, {}};
         const void* cen[3] = {r, dinv, yprev};
         KScope ks(c.prof, c.stream, K_PCG_CHEB, nb(c, KIND == 1 ? 3 : (KIND == 2 ? 4 : 5), 4));
         if constexpr (KIND == 1) {
