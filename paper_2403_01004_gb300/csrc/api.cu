@@ -796,13 +796,16 @@ int be_pcg_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, c
             // once the float64 residual confirms it (PB_MIXED_FP64_RESIDUAL=1: float64 throughout)
             const bool df_residual = o.mixed_precision && c.prec == PB_FP64 && o.fixed_iters <= 0 &&
                                      c.kind == PB_TC_ANISO && !env_on("PB_MIXED_FP64_RESIDUAL");
+            // iterative refinement (mixed precision): its outer residuals need no D^-1
+            const bool refine = o.mixed_precision && c.prec == PB_FP64 && o.fixed_iters <= 0;
             bool exact = true;      // the residual at hand is the float64 one
             auto init = [&](bool want_exact = false) {
                 *c.h_pcg = hs0;
                 PB_CUDA_TRY(cudaMemcpyAsync(c.d_pcg, c.h_pcg, sizeof(PcgScalars), cudaMemcpyHostToDevice, c.stream));
                 exact = want_exact || !df_residual;
-                if (exact) ops->pcg_init(c, u, c.buf[0], dt_c);
-                else mixed_residual(c, u, c.buf[0], dt_c);
+                if (!exact) mixed_residual(c, u, c.buf[0], dt_c);
+                else if (refine) ops->pcg_residual(c, u, c.buf[0], dt_c);
+                else ops->pcg_init(c, u, c.buf[0], dt_c);
                 PB_CUDA_TRY(cudaMemcpyAsync(c.h_pcg, c.d_pcg, sizeof(PcgScalars), cudaMemcpyDeviceToHost, c.stream));
                 sync(c);
                 return c.h_pcg->rr;
@@ -822,7 +825,6 @@ int be_pcg_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, c
                 init();
             }
             ChebPlan plan;
-            const bool refine = o.mixed_precision && c.prec == PB_FP64 && o.fixed_iters <= 0;
             if (cheb) {
                 plan = cheb_plan(ops->cheb_bound(c, dt_c), o.pc_degree);
                 if (!refine) ops->pcg_precond(c, plan, dt_c);      // z_0 = P r_0 and <r_0, z_0>
@@ -851,7 +853,8 @@ int be_pcg_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, c
                     // factor 4 of margin for the float32 rounding of the correction
                     double tau = o.inner_rtol;
                     const double need = 0.25 * std::sqrt(now.tol2 * now.bb / now.rr);
-                    if (need > tau) tau = std::min(need, 0.5);
+                    const bool last = need > tau;
+                    if (last) tau = std::min(need, 0.5);
                     int status = 0;
                     inner += mixed_inner(c, u, dt_c, tau, o.max_iter - inner, o.check_every, &status,
                                          cheb ? &plan : nullptr);
@@ -860,7 +863,9 @@ int be_pcg_advance(pb_ctx* h, void* u, double dt, const pb_advance_opts* opts, c
                         c.h_pcg->done = 2;
                         break;
                     }
-                    init();
+                    // after a correction meant to meet the outer test, the float64 residual decides
+                    // at once (it would confirm the double-float one anyway)
+                    init(last && status == 0);
                 }
                 c.h_pcg->iter = inner;
             } else {

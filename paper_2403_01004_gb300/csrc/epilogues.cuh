@@ -231,8 +231,10 @@ struct EpiStage2 {
 
 // PCG set-up on the system S x = b, S = M - dt A, b = M u^n (the record's 4th word is M = 1/w):
 //   r = b - S x = M (u^n - x) + dt A x,  D^-1 = 1/(M - dt diag A),  and the sums <r, D^-1 r>,
-//   <r, r>, <b, b>; the last block initialises the scalar state.
-template <class P>
+//   <r, r>, <b, b>; the last block initialises the scalar state.  FULL = false forms r, <r, r> and
+//   <b, b> only (<r, D^-1 r> = 0): the outer residual of an iterative refinement, which needs no
+//   D^-1 (and skips its division, costly in float64 on GB300).
+template <class P, bool FULL = true>
 struct EpiPcgInit {
     using A = typename P::A;
     using S = typename P::S;
@@ -250,16 +252,18 @@ struct EpiPcgInit {
     double acc[3];
     __device__ void init() { acc[0] = acc[1] = acc[2] = 0.0; }
     __device__ bool skip() const { return false; }
-    __device__ Pre prefetch(long long idx) const { return Pre{cvt<A>(un[idx]), (A)__ldg(adiag + idx)}; }
+    __device__ Pre prefetch(long long idx) const { return Pre{cvt<A>(un[idx]), FULL ? (A)__ldg(adiag + idx) : A(0)}; }
     __device__ void apply(long long idx, A Au, A m, A x, const Pre& p) {
         const S rs = cvt<S>(m * (p.un - x) + dt * Au);
-        const S ds = cvt<S>(A(1) / (m - dt * p.ad));
         r[idx] = rs;
-        dinv[idx] = ds;
         const double rd = (double)cvt<A>(rs);
-        const double z = (double)cvt<A>(cvt<S>(cvt<A>(ds) * cvt<A>(rs)));
         const double b = (double)(m * p.un);
-        acc[0] += rd * z;
+        if constexpr (FULL) {
+            const S ds = cvt<S>(A(1) / (m - dt * p.ad));
+            dinv[idx] = ds;
+            const double z = (double)cvt<A>(cvt<S>(cvt<A>(ds) * cvt<A>(rs)));
+            acc[0] += rd * z;
+        }
         acc[1] += rd * rd;
         acc[2] += b * b;
     }

@@ -40,6 +40,9 @@ public:
                        void* out, const StageCoef& k) = 0;
     // PCG: set-up from x (in place) and u^n; one SpMV + update iteration
     virtual void pcg_init(Ctx& c, const void* x, const void* un, double dt) = 0;
+    // r = b - S x with <r, r>, <b, b> and the stopping decision only (no D^-1, no <r, D^-1 r>):
+    // the outer residual of mixed-precision Backward Euler
+    virtual void pcg_residual(Ctx& c, const void* x, const void* un, double dt) = 0;
     virtual void pcg_iter(Ctx& c, void* x, int parity, double dt) = 0;
     // Chebyshev-preconditioned PCG: the bound b of the spectrum of D^-1 S for step dt (host
     // value); z = P r with <r, z> and beta; one iteration (product, update, preconditioner)

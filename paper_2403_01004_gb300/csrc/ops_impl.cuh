@@ -338,6 +338,13 @@ public:
         march(c, c.coef_be, LoadState<P>{static_cast<const S*>(x)}, ep);
     }
 
+    void pcg_residual(Ctx& c, const void* x, const void* un, double dt) override {
+        KScope ks(c.prof, c.stream, K_PCG_INIT, nb(c, 3, 4));
+        EpiPcgInit<P, false> ep{static_cast<const S*>(un), static_cast<S*>(c.r), nullptr, nullptr, c.d_pcg,
+                                static_cast<double*>(c.partials), c.counter, c.grid.nblocks, (A)dt};
+        march(c, c.coef_be, LoadState<P>{static_cast<const S*>(x)}, ep);
+    }
+
     void pcg_iter(Ctx& c, void* x, int parity, double dt) override {
         S* pold = static_cast<S*>(c.p[parity]);
         S* pnew = static_cast<S*>(c.p[parity ^ 1]);
