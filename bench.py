@@ -212,49 +212,74 @@ def run_ours(args):
         return step_tc(tc_fields, u_src) + step_visc(vi_fields, v_src)
 
     # end to end: every input from pinned host memory and both results back, inside the timed
-    # region, pipelined as a user advancing many steps would: the viscosity inputs travel on a
-    # copy stream while conduction computes, and the conduction result plus the next step's
-    # conduction inputs while viscosity computes (the first step of a timed run copies its own
-    # conduction inputs, the last prefetches none)
+    # region, pipelined as a user advancing many steps would.  An operator's inputs are consumed
+    # by its coefficient update and the copy of its initial state, so the next step's inputs of
+    # that operator travel on a copy stream while its super steps run, and each result travels
+    # back while the next operator (or the next step) computes.  The first step of a timed run
+    # copies its own inputs (the viscosity inputs while conduction computes), the last prefetches
+    # none; the last result is waited for inside the timed region.
     copy_stream = torch.cuda.Stream()
-    e2e_state = {"left": 0, "tc_ready": None}
+    e2e_state = {"left": 0, "tc_ready": None, "v_ready": None, "u_out": None, "v_out": None}
 
-    def copy_tc_inputs():
+    def on_copy_stream(after, copies):
+        """Runs copies on the copy stream after event `after` of the main stream; returns the
+        event that marks their completion."""
+        copy_stream.wait_event(after)
         with torch.cuda.stream(copy_stream):
-            for k in ("T0", "n"):
-                d_tc[k].copy_(h_tc[k], non_blocking=True)
-            for a in range(3):
-                d_tc["B"][a].copy_(h_tc["B"][a], non_blocking=True)
-            d_u0.copy_(h_u, non_blocking=True)
+            copies()
             ev = torch.cuda.Event()
             ev.record(copy_stream)
+        return ev
+
+    def copy_tc_in():
+        for k in ("T0", "n"):
+            d_tc[k].copy_(h_tc[k], non_blocking=True)
+        for a in range(3):
+            d_tc["B"][a].copy_(h_tc["B"][a], non_blocking=True)
+        d_u0.copy_(h_u, non_blocking=True)
+
+    def copy_visc_in():
+        for a in range(3):
+            d_vi["rho"][a].copy_(h_vi["rho"][a], non_blocking=True)
+            d_vi["nu"][a].copy_(h_vi["nu"][a], non_blocking=True)
+        d_v0.copy_(h_v, non_blocking=True)
+
+    def marker(stream_):
+        ev = torch.cuda.Event()
+        ev.record(stream_)
         return ev
 
     def e2e_step():
         main = torch.cuda.current_stream()
         e2e_state["left"] -= 1
-        copy_stream.wait_stream(main)
-        ev_tc = e2e_state["tc_ready"] or copy_tc_inputs()
-        e2e_state["tc_ready"] = None
-        ev_v, ev_u = torch.cuda.Event(), torch.cuda.Event()
-        with torch.cuda.stream(copy_stream):
-            for a in range(3):
-                d_vi["rho"][a].copy_(h_vi["rho"][a], non_blocking=True)
-                d_vi["nu"][a].copy_(h_vi["nu"][a], non_blocking=True)
-            d_v0.copy_(h_v, non_blocking=True)
-            ev_v.record(copy_stream)
+        more = e2e_state["left"] > 0
+        now = marker(main)
+        ev_tc = e2e_state["tc_ready"] or on_copy_stream(now, copy_tc_in)
+        ev_v = e2e_state["v_ready"] or on_copy_stream(now, copy_visc_in)
+        # conduction: its inputs are consumed by the update and the state copy
         main.wait_event(ev_tc)
-        units = step_tc(d_tc, d_u0)
-        ev_u.record(main)
-        copy_stream.wait_event(ev_u)
-        with torch.cuda.stream(copy_stream):
-            out_u.copy_(u, non_blocking=True)
-        if e2e_state["left"] > 0:
-            e2e_state["tc_ready"] = copy_tc_inputs()
+        if e2e_state["u_out"] is not None:
+            main.wait_event(e2e_state["u_out"])       # the previous result has left u
+        u.copy_(d_u0)
+        pb.parabolic_update(ctx_tc, d_tc)
+        dt = wl["ratio"] * pb.parabolic_dt_explicit(ctx_tc)
+        e2e_state["tc_ready"] = on_copy_stream(marker(main), copy_tc_in) if more else None
+        stats["tc"] = pb.rkl2_advance(ctx_tc, u, dt, scheme=args.scheme, use_ptl=True)
+        units = n_tc * stats["tc"]["total_stages"]
+        e2e_state["u_out"] = on_copy_stream(marker(main), lambda: out_u.copy_(u, non_blocking=True))
+        # viscosity, the same way
         main.wait_event(ev_v)
-        units += step_visc(d_vi, d_v0)
-        out_v.copy_(v, non_blocking=True)
-        main.wait_stream(copy_stream)
+        if e2e_state["v_out"] is not None:
+            main.wait_event(e2e_state["v_out"])
+        v.copy_(d_v0)
+        pb.parabolic_update(ctx_v, d_vi)
+        dt = wl["ratio"] * pb.parabolic_dt_explicit(ctx_v)
+        e2e_state["v_ready"] = on_copy_stream(marker(main), copy_visc_in) if more else None
+        stats["visc"] = pb.rkl2_advance(ctx_v, v, dt, scheme=args.scheme, use_ptl=True)
+        units += n_v * stats["visc"]["total_stages"]
+        e2e_state["v_out"] = on_copy_stream(marker(main), lambda: out_v.copy_(v, non_blocking=True))
+        if not more:
+            main.wait_stream(copy_stream)
         return units
 
     stream = torch.cuda.current_stream()
@@ -302,12 +327,16 @@ def run_ours(args):
     if not args.no_e2e:
         e2e_state["left"] = 1
         e2e_step()
-        e2e_state["left"] = args.steps
+        e2e_state.update(left=args.steps, u_out=None, v_out=None)
         units_e, ms_e, _ = timed(e2e_step, args.steps)
         h2d = sum(t.numel() * t.element_size() for t in [h_tc["T0"], h_tc["n"], *h_tc["B"], *h_vi["rho"], *h_vi["nu"], h_u, h_v])
         d2h = out_u.numel() * out_u.element_size() + out_v.numel() * out_v.element_size()
+        # every step starts from the same inputs: the results copied back must equal the device-
+        # resident run's bit for bit (a check that no copy overtook its consumer)
+        same = bool(torch.equal(out_u.to(result["tc"].device), result["tc"]) and
+                    torch.equal(out_v.to(result["visc"].device), result["visc"]))
         e2e = {"value": units_e / (ms_e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": ms_e / args.steps}
+               "d2h_bytes_per_step": d2h, "ms_per_step": ms_e / args.steps, "results_equal_device_run": same}
 
     # dominant kernel class of the timed region and its roofline against measured HBM bandwidth
     dom = max(prof, key=lambda p: p["total_ms"])
