@@ -250,11 +250,14 @@ PB_API int rkl2_advance_relag(pb_ctx* ctx, void* u_dev, double dt, const pb_adva
 /* Advances u (device, in place) over dt with Backward Euler, each cycle solving
  * (M - dt_c A) x = M u (M = diag(1/w), F = w A u) by point-Jacobi PCG from x0 = u, or from
  * x0_dev (device, ctx precision) on the first cycle when it is not NULL.  Supported for
- * PB_FP64 and PB_FP32 (float vectors, float64 dot products).  stats may be NULL.
- * With opts->mixed_precision on a PB_FP64 conduction context the outer residuals that drive
- * the refinements are computed in double-float arithmetic (about 48 bits, on the float32
- * pipes), and a cycle stops only when the float64 residual meets rtol; environment
- * PB_MIXED_FP64_RESIDUAL=1 (read at each call) uses float64 residuals throughout.
+ * PB_FP64 and PB_FP32 (float vectors; the dot products sum the exact float products in
+ * double-float, about 44 bits).  stats may be NULL.
+ * With opts->mixed_precision on a PB_FP64 context each cycle is solved by iterative refinement:
+ * float32 PCG corrections to opts->inner_rtol driven by outer residuals.  On a conduction
+ * context those residuals are computed in double-float arithmetic (about 48 bits, on the float32
+ * pipes), except the one after the correction meant to meet rtol, which is float64; a cycle
+ * stops only when a float64 residual meets rtol.  Environment PB_MIXED_FP64_RESIDUAL=1 (read at
+ * each call) uses float64 residuals throughout.
  * With mixed_precision the PTL decision is taken on a float32 view of the state (F in float32,
  * the arg-max compared in float), as the float32 contexts take it.
  * opts->precond = PB_PC_CHEBYSHEV preconditions the PCG polynomially (with mixed_precision, the
